@@ -1,0 +1,279 @@
+/*
+ * streamgb — field-line advection on one GB300 (sm_103a), C ABI.
+ *
+ * The calls follow the problem statement of Zellmann et al., "Streami: An MPI
+ * Data-Parallel Library to Compute Field Lines on GPUs":
+ *   - a vector field made of macrocells (here: bricks) with a halo, created
+ *     per brick or from a global array (Sec. 3.1.1, Sec. 3.3);
+ *   - seeds given as positions, each tracked by a unique ID (Sec. 3.1.2);
+ *   - step / trace / getLines of the Tracer (Sec. 3.2, Fig. 4, Listing 2),
+ *     in streamline or streakline mode (the Mode enumeration of Fig. 4).
+ *
+ * Conventions
+ *   - Every call returns sg_status: SG_OK (0) or a negative error.  No call
+ *     throws or aborts.  sg_last_error() gives a message for the last error
+ *     raised on the calling host thread.
+ *   - Handles are opaque.  Large device buffers are owned by the caller: each
+ *     *_required_bytes query comes before the matching *_create, which carves
+ *     its state out of the caller's buffer and allocates no device memory of
+ *     its own (except the CUDA graph objects of a tracer).  The caller keeps
+ *     the buffer alive until the handle is destroyed.
+ *   - Streams are cudaStream_t passed as void* (0 = legacy default stream).
+ *     A call is asynchronous on its stream unless it says otherwise; it
+ *     returns before the GPU work ends.  Host pointers given to an
+ *     asynchronous call must stay valid until the stream reaches that point.
+ *   - Positions are world coordinates, float32 xyz triples (AoS).  Index
+ *     space: world = origin + spacing * index per axis; the sampled domain is
+ *     the closed box [0, dims-1] per axis.
+ *   - "host or device" pointers are classified with cudaPointerGetAttributes.
+ *     Pointers that a kernel writes or reads directly must be device memory or
+ *     page-locked host memory (cudaHostAlloc / cudaHostRegister); pageable
+ *     host memory is accepted only where the argument says so.
+ */
+#ifndef STREAMGB_H
+#define STREAMGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t sg_status;
+
+enum {
+    SG_OK = 0,
+    SG_ERR_INVALID_ARG = -1,   /* a NULL handle, a bad size, an unsupported combination */
+    SG_ERR_OOM = -2,           /* the caller's buffer is smaller than *_required_bytes */
+    SG_ERR_CUDA = -3,          /* a CUDA runtime call failed; see sg_last_error */
+    SG_ERR_ROUND_LIMIT = -4,   /* a trace hit its round cap with particles left */
+    SG_ERR_TIMEOUT = -5,       /* a bounded wait ran out */
+    SG_ERR_STATE = -6,         /* the call does not fit the object's state */
+    SG_ERR_UNSUPPORTED = -7    /* not built for this mode / dtype / layout */
+};
+
+/* Field storage type.  SG_F32 stores the samples as given; SG_BF16 and SG_F16
+ * store code = round-to-nearest-even(v / s_b) with one scale s_b per brick,
+ * s_b the smallest power of two >= the largest finite |component| among the
+ * brick's stored samples (ghosts included), and decode as code * s_b.
+ * Interpolation and integration are FP32 in every case. */
+enum { SG_F32 = 0, SG_BF16 = 1, SG_F16 = 2 };
+
+/* Sample layout inside a brick (both: 16 B per FP32 sample, 8 B per BF16/FP16
+ * sample, components x, y, z and one pad).  LINEAR is x-fastest; TILED4 groups
+ * 4x4x4 samples contiguously (tile-major, x-fastest inside a tile). */
+enum { SG_LAYOUT_LINEAR = 0, SG_LAYOUT_TILED4 = 1 };
+
+/* Line status (uint8 per line).  Bit 7 (SG_LINE_TIE) marks a boundary tie: a
+ * line that stopped by EXIT with its offending point less than tie_cells
+ * outside the domain, or by STAGNANT with (eps - |v|)/eps < tie_eps_rel. */
+enum {
+    SG_LINE_ACTIVE = 0,    /* not stopped yet (after sg_tracer_step)          */
+    SG_LINE_MAXSTEPS = 1,  /* reached max_steps                                */
+    SG_LINE_EXIT = 2,      /* a stage point or the new position left the domain */
+    SG_LINE_STAGNANT = 3,  /* |v(P0)| < eps in world units, before a step       */
+    SG_LINE_NANFIELD = 4,  /* a sample was not finite                           */
+    SG_LINE_OUT = 5,       /* the seed lies outside the domain (no vertex)      */
+    SG_LINE_HALO = 6,      /* a stage point left the brick's ghost shell: dt *
+                              max speed exceeded one cell                        */
+    SG_LINE_TIE = 0x80
+};
+
+enum { SG_STREAMLINE = 0, SG_STREAKLINE = 1 };
+
+/* Advection kernel of a streamline tracer. */
+enum {
+    SG_KERNEL_PERSISTENT = 0,  /* bricked field; persistent warps refill lanes from
+                                  per-brick queues; rounds run as one CUDA graph  */
+    SG_KERNEL_PER_SEED = 1,    /* one thread per seed to termination on a global
+                                  FP32 field (layout SG_FIELD_GLOBAL only)         */
+    SG_KERNEL_PER_STEP = 2     /* Listing 1: one launch per advection step, one
+                                  thread per particle, forwarding between launches */
+};
+
+typedef struct sg_context sg_context;
+typedef struct sg_field sg_field;
+typedef struct sg_tracer sg_tracer;
+typedef struct sg_batch sg_batch;
+
+/* Copies the last error message of the calling thread into buf (NUL-terminated,
+ * truncated to n bytes).  Returns the length of the full message. */
+size_t sg_last_error(char *buf, size_t n);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int32_t sg_version(void);
+
+/* ------------------------------------------------------------------ context */
+
+/* Makes `device` current and records its properties (SM count, shared memory,
+ * L2 size).  One context per device; it holds no device memory. */
+sg_status sg_context_create(int32_t device, sg_context **out);
+sg_status sg_context_destroy(sg_context *ctx);
+/* Number of SMs of the context's device (for grid sizing by callers). */
+sg_status sg_context_sm_count(const sg_context *ctx, int32_t *out);
+
+/* -------------------------------------------------------------------- field */
+
+/* A structured vector field on a uniform grid, split into a uniform grid of
+ * bricks (the paper's macrocells, Sec. 3.1.1 and Sec. 3.3).
+ *
+ * Brick b = (bx, by, bz) owns n = ceil((dims-1)/bricks) cells per axis, the
+ * index interval [b*n, b*n+n), and the last brick also the upper face; a
+ * position on an interior face belongs to the upper brick (this is the
+ * field's destinationID).  Each brick stores the samples b*n-1 .. b*n+n+1
+ * (n+3 per axis, clamped to [0, dims-1]): the owned cells plus a one-cell
+ * ghost shell, the macrocell's halo.  A step whose displacement is at most
+ * one cell (dt * max speed <= 1) samples only its own brick.
+ *
+ * layout SG_FIELD_GLOBAL (bricks must be 1x1x1, dtype SG_F32) instead keeps
+ * the paper's plain float3 AoS voxel array, sampled by offsets into it; it
+ * is the field of SG_KERNEL_PER_SEED.
+ *
+ * n_slots resident copies (time slices) share the geometry; steady fields
+ * use 1.  Unsteady fields map time slice s (time s * slice_dt) to slot
+ * s % n_slots when it is streamed in. */
+enum { SG_FIELD_GLOBAL = 16 };
+
+typedef struct {
+    int64_t dims[3];      /* samples per axis, each >= 2                        */
+    double origin[3];     /* world position of sample (0, 0, 0)                 */
+    double spacing[3];    /* world distance between samples, > 0                */
+    int32_t bricks[3];    /* bricks per axis, >= 1; the last brick must own a cell */
+    int32_t ghost;        /* ghost layers; must be 1                            */
+    int32_t dtype;        /* SG_F32, SG_BF16, SG_F16                            */
+    int32_t layout;       /* SG_LAYOUT_LINEAR, SG_LAYOUT_TILED4, SG_FIELD_GLOBAL */
+    int32_t n_slots;      /* resident slices, >= 1                              */
+    double slice_dt;      /* time between slices (unsteady fields), > 0         */
+} sg_field_desc;
+
+/* Device bytes needed by a field with this description (all slots plus a
+ * staging area of one global FP32 slice for streamed slices). */
+sg_status sg_field_required_bytes(const sg_field_desc *desc, size_t *bytes);
+
+/* Creates a field in the caller's device buffer `storage` of `bytes` bytes
+ * (256-byte aligned).  The field does not own the buffer. */
+sg_status sg_field_create(sg_context *ctx, const sg_field_desc *desc, void *storage, size_t bytes,
+                          sg_field **out);
+sg_status sg_field_destroy(sg_field *f);
+
+/* Owned cells per brick per axis (n above). */
+sg_status sg_field_brick_cells(const sg_field *f, int64_t n_out[3]);
+
+/* Sets slot `slot` from a global FP32 AoS array [dims2][dims1][dims0][3]
+ * (device or page-locked host memory): cuts the bricks, fills the ghost
+ * shells and encodes BF16/FP16 with per-brick scales.  Asynchronous. */
+sg_status sg_field_set_global(sg_field *f, int32_t slot, const float *vec3, void *stream);
+
+/* Sets one brick of slot `slot` from its own (n+3)^3 FP32 AoS samples,
+ * ghost shell included, as the application holds it (device or page-locked
+ * host memory); samples are those at global indices b*n-1 .. b*n+n+1 per
+ * axis, which the caller clamps (or fills) at the domain faces itself.
+ * Asynchronous. */
+sg_status sg_field_set_brick(sg_field *f, int32_t slot, int32_t bx, int32_t by, int32_t bz,
+                             const float *vec3_with_halo, void *stream);
+
+/* Streams time slice `slice` from page-locked host memory (global FP32 AoS)
+ * into slot slice % n_slots on `stream`, and records that the slot holds the
+ * slice once the stream reaches the end of the copy.  A tracer step that
+ * needs the slice waits for it on its own stream (cudaStreamWaitEvent). */
+sg_status sg_field_stream_slice(sg_field *f, int32_t slice, const float *pinned_host, void *stream);
+
+/* Largest |v / spacing| over the stored (decoded) samples of `slot`, in cells
+ * per unit time; dt = h / max_speed makes every step at most h cells.
+ * Synchronous on `stream`. */
+sg_status sg_field_max_speed(sg_field *f, int32_t slot, double *cells_per_time, void *stream);
+
+/* Copies brick (bx,by,bz) of `slot` back in a canonical form: FP32 stores give
+ * (n+3)^3*3 floats, BF16/FP16 stores give (n+3)^3*3 uint16 codes (z, y, x,
+ * component order) and the brick scale.  `out` is host memory of at least
+ * (n+3)^3*3*(4 or 2) bytes.  Synchronous. */
+sg_status sg_field_read_brick(sg_field *f, int32_t slot, int32_t bx, int32_t by, int32_t bz,
+                              void *out, float *scale, void *stream);
+
+/* ------------------------------------------------------------------- tracer */
+
+typedef struct {
+    int32_t mode;          /* SG_STREAMLINE or SG_STREAKLINE                       */
+    int32_t kernel;        /* SG_KERNEL_* (streamlines)                             */
+    double dt;             /* time step (k_i = dt * v / spacing, in cells)          */
+    int32_t max_steps;     /* streamlines: steps per line (>= 0)                    */
+    float eps;             /* stop when |v(P0)| < eps (world units); 1e-6 typical   */
+    float tie_cells;       /* tie threshold for EXIT (cells); 0 turns ties off      */
+    float tie_eps_rel;     /* tie threshold for STAGNANT (relative)                 */
+    int32_t inject_steps;  /* streaklines: particles released per release point     */
+    /* schedule of the persistent kernel (0 = default) */
+    int32_t block_size;    /* threads per CTA (multiple of 32, <= 1024)              */
+    int32_t blocks_per_sm; /* CTAs per SM of the persistent grid                     */
+    int32_t steps_per_round; /* steps a particle may take in one round before it is
+                                re-queued in its own brick                          */
+    int32_t max_rounds;    /* round cap of one trace / step call                     */
+} sg_tracer_params;
+
+/* Fills p with the defaults (streamline, persistent kernel, eps 1e-6,
+ * tie_cells 1e-3, tie_eps_rel 1e-3, automatic schedule). */
+sg_status sg_tracer_params_default(sg_tracer_params *p);
+
+/* Device bytes of a tracer for up to `capacity` seeds (streamlines) or
+ * release points (streaklines): particle queues, the per-line vertex slabs
+ * (capacity * (max_steps+1) * 12 B for streamlines), per-line lengths and
+ * status, and the scan scratch of the compaction. */
+sg_status sg_tracer_required_bytes(const sg_context *ctx, const sg_field *f, const sg_tracer_params *p,
+                                   int64_t capacity, size_t *bytes);
+
+sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tracer_params *p, int64_t capacity,
+                           void *workspace, size_t bytes, sg_tracer **out);
+sg_status sg_tracer_destroy(sg_tracer *t);
+
+/* Seeds (streamlines) or release points (streaklines): n world xyz float32
+ * triples, host (pageable or page-locked) or device memory; n <= capacity.
+ * Line i is seed i (the unique particle ID of Sec. 3.1.2).  Bins the seeds
+ * into per-brick queues and writes each line's first vertex; a seed outside
+ * the domain gets status SG_LINE_OUT and no vertex.  Streaklines release
+ * birth 0 at every release point.  Resets any previous trace.  Asynchronous. */
+sg_status sg_tracer_upload_seeds(sg_tracer *t, const float *xyz, int64_t n, void *stream);
+
+/* Advances by n_steps steps (Listing 2's step(), called n_steps times):
+ * streamlines advance every active line by up to n_steps more steps;
+ * streaklines advance every released particle by one step of the time-
+ * dependent field and then release the next birth, n_steps times.
+ * any_active (nullable, host) receives 1 if a particle can still move; when
+ * it is non-NULL the call synchronises the stream.  Returns
+ * SG_ERR_ROUND_LIMIT if the round cap stopped the call early. */
+sg_status sg_tracer_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, void *stream);
+
+/* Streamlines: advances until every line has stopped (Sec. 3.2's trace()).
+ * The persistent kernel runs as one CUDA graph launch whose conditional
+ * while-node repeats rounds until the queues are empty.  Asynchronous;
+ * sg_tracer_check reports a round-cap stop afterwards. */
+sg_status sg_tracer_trace(sg_tracer *t, void *stream);
+
+/* Synchronises `stream` and returns SG_ERR_ROUND_LIMIT if a previous
+ * asynchronous trace stopped at its round cap, else SG_OK.  rounds (nullable)
+ * receives the number of rounds of the last trace. */
+sg_status sg_tracer_check(sg_tracer *t, int32_t *rounds, void *stream);
+
+/* Line readback (getLines of Fig. 4), compacted to CSR: line i's vertices
+ * are vertices[offsets[i] .. offsets[i+1]) (world xyz float32).  For
+ * streamlines there is one line per seed; for streaklines one line per run of
+ * consecutive live particles of a release point, oldest birth first, and
+ * line_source gives its release point.  Two calls: with offsets and vertices
+ * NULL it only returns n_lines and n_vertices (synchronising the stream);
+ * then with buffers of n_lines+1 int64 offsets, 3*n_vertices floats, n_lines
+ * status bytes, n_lines float margins and n_lines int32 sources (each
+ * nullable, device or page-locked host memory).  margin: EXIT distance
+ * outside (cells), STAGNANT relative margin, else +inf.  Asynchronous when
+ * the buffers are given. */
+sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t *n_vertices, int64_t *offsets,
+                              float *vertices, uint8_t *status, float *margin, int32_t *line_source,
+                              void *stream);
+
+/* Successful RK4 steps of the current trace summed over all lines (the unit of
+ * the particle-steps/s metric).  Synchronous. */
+sg_status sg_tracer_total_steps(sg_tracer *t, int64_t *steps, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STREAMGB_H */

@@ -1,0 +1,248 @@
+"""Python objects over the C ABI: PyTorch provides device memory and streams.
+
+Every step of the hot path runs in libstreamgb's kernels; this module only
+allocates the caller-owned buffers the C ABI asks for and marshals pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import call
+
+DTYPES = {"f32": L.SG_F32, "bf16": L.SG_BF16, "f16": L.SG_F16}
+LAYOUTS = {"linear": L.SG_LAYOUT_LINEAR, "tiled4": L.SG_LAYOUT_TILED4, "global": L.SG_FIELD_GLOBAL}
+KERNELS = {"persistent": L.SG_KERNEL_PERSISTENT, "per_seed": L.SG_KERNEL_PER_SEED, "per_step": L.SG_KERNEL_PER_STEP}
+STATUS_NAMES = {0: "ACTIVE", 1: "MAXSTEPS", 2: "EXIT", 3: "STAGNANT", 4: "NANFIELD", 5: "OUT", 6: "HALO"}
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(x) -> ctypes.c_void_p:
+    if x is None:
+        return ctypes.c_void_p(None)
+    if isinstance(x, torch.Tensor):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(int(x))
+
+
+class Context:
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        call("sg_context_create", self.device, ctypes.byref(h))
+        self.h = h
+        n = ctypes.c_int32()
+        call("sg_context_sm_count", self.h, ctypes.byref(n))
+        self.sm_count = n.value
+
+    def close(self):
+        if self.h:
+            L.lib().sg_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def field_desc(dims, origin, spacing, bricks=(1, 1, 1), dtype="f32", layout="linear", n_slots=1,
+               slice_dt=1.0) -> L.sg_field_desc:
+    d = L.sg_field_desc()
+    for a in range(3):
+        d.dims[a] = int(dims[a])
+        d.origin[a] = float(origin[a])
+        d.spacing[a] = float(spacing[a])
+        d.bricks[a] = int(bricks[a])
+    d.ghost = 1
+    d.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    d.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    d.n_slots = int(n_slots)
+    d.slice_dt = float(slice_dt)
+    return d
+
+
+class Field:
+    """A bricked (or global float3) vector field in a torch-owned device buffer."""
+
+    def __init__(self, ctx: Context, dims, origin, spacing, bricks=(1, 1, 1), dtype="f32", layout="linear",
+                 n_slots=1, slice_dt=1.0):
+        self.ctx = ctx
+        self.desc = field_desc(dims, origin, spacing, bricks, dtype, layout, n_slots, slice_dt)
+        nbytes = ctypes.c_size_t()
+        call("sg_field_required_bytes", ctypes.byref(self.desc), ctypes.byref(nbytes))
+        self.nbytes = nbytes.value
+        self.storage = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=f"cuda:{ctx.device}")
+        h = ctypes.c_void_p()
+        call("sg_field_create", ctx.h, ctypes.byref(self.desc), _ptr(self.storage), self.nbytes, ctypes.byref(h))
+        self.h = h
+        self.dims = tuple(int(x) for x in dims)
+        self.origin = tuple(float(x) for x in origin)
+        self.spacing = tuple(float(x) for x in spacing)
+        self.bricks = tuple(int(x) for x in bricks)
+        self.dtype = dtype
+
+    def brick_cells(self):
+        n = (ctypes.c_int64 * 3)()
+        call("sg_field_brick_cells", self.h, n)
+        return tuple(n)
+
+    def set_global(self, vec3, slot: int = 0, stream=None):
+        """vec3: float32 [nz][ny][nx][3] on the device or in page-locked host memory."""
+        assert vec3.dtype == torch.float32 and vec3.is_contiguous()
+        call("sg_field_set_global", self.h, slot, _ptr(vec3), _stream(stream))
+
+    def set_brick(self, bx, by, bz, vec3_with_halo, slot: int = 0, stream=None):
+        assert vec3_with_halo.dtype == torch.float32 and vec3_with_halo.is_contiguous()
+        call("sg_field_set_brick", self.h, slot, bx, by, bz, _ptr(vec3_with_halo), _stream(stream))
+
+    def stream_slice(self, slice_index: int, pinned_host, stream=None):
+        call("sg_field_stream_slice", self.h, slice_index, _ptr(pinned_host), _stream(stream))
+
+    def max_speed(self, slot: int = 0, stream=None) -> float:
+        v = ctypes.c_double()
+        call("sg_field_max_speed", self.h, slot, ctypes.byref(v), _stream(stream))
+        return v.value
+
+    def read_brick(self, bx, by, bz, slot: int = 0, stream=None):
+        n = self.brick_cells()
+        shape = (n[2] + 3, n[1] + 3, n[0] + 3, 3)
+        out = np.zeros(shape, dtype=np.float32 if self.desc.dtype == L.SG_F32 else np.uint16)
+        sc = ctypes.c_float()
+        call("sg_field_read_brick", self.h, slot, bx, by, bz, _ptr(out), ctypes.byref(sc), _stream(stream))
+        return out, sc.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib().sg_field_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Lines:
+    offsets: torch.Tensor      # int64 [n_lines + 1]
+    vertices: torch.Tensor     # float32 [n_vertices, 3] world
+    status: torch.Tensor       # uint8 [n_lines]
+    margin: torch.Tensor       # float32 [n_lines]
+    source: torch.Tensor       # int32 [n_lines]
+
+    def lengths(self):
+        return self.offsets[1:] - self.offsets[:-1]
+
+
+def tracer_params(dt, max_steps=1000, mode="streamline", kernel="persistent", eps=1e-6, tie_cells=1e-3,
+                  tie_eps_rel=1e-3, inject_steps=1, block_size=0, blocks_per_sm=0, steps_per_round=0,
+                  max_rounds=0) -> L.sg_tracer_params:
+    p = L.sg_tracer_params()
+    call("sg_tracer_params_default", ctypes.byref(p))
+    p.mode = L.SG_STREAMLINE if mode == "streamline" else L.SG_STREAKLINE
+    p.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    p.dt = float(dt)
+    p.max_steps = int(max_steps)
+    p.eps = float(eps)
+    p.tie_cells = float(tie_cells)
+    p.tie_eps_rel = float(tie_eps_rel)
+    p.inject_steps = int(inject_steps)
+    p.block_size = int(block_size)
+    p.blocks_per_sm = int(blocks_per_sm)
+    p.steps_per_round = int(steps_per_round)
+    p.max_rounds = int(max_rounds)
+    return p
+
+
+class Tracer:
+    """Streamline or streakline tracer (the paper's Tracer: step / trace / getLines)."""
+
+    def __init__(self, ctx: Context, field: Field, capacity: int, **params):
+        self.ctx = ctx
+        self.field = field
+        self.params = tracer_params(**params)
+        self.capacity = int(capacity)
+        nbytes = ctypes.c_size_t()
+        call("sg_tracer_required_bytes", ctx.h, field.h, ctypes.byref(self.params), self.capacity,
+             ctypes.byref(nbytes))
+        self.nbytes = nbytes.value
+        self.workspace = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=f"cuda:{ctx.device}")
+        h = ctypes.c_void_p()
+        call("sg_tracer_create", ctx.h, field.h, ctypes.byref(self.params), self.capacity, _ptr(self.workspace),
+             self.nbytes, ctypes.byref(h))
+        self.h = h
+        self._seeds = None
+
+    def upload_seeds(self, xyz, stream=None):
+        """xyz: (n, 3) float32 world positions (torch tensor on any device, or numpy)."""
+        if isinstance(xyz, np.ndarray):
+            xyz = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.float32))
+        assert xyz.dtype == torch.float32
+        xyz = xyz.contiguous()
+        self._seeds = xyz           # keep alive until the copy is done
+        call("sg_tracer_upload_seeds", self.h, _ptr(xyz), int(xyz.shape[0]), _stream(stream))
+
+    def step(self, n_steps: int = 1, sync: bool = True, stream=None):
+        act = ctypes.c_int32(0)
+        call("sg_tracer_step", self.h, int(n_steps), ctypes.byref(act) if sync else None, _stream(stream))
+        return bool(act.value) if sync else None
+
+    def trace(self, stream=None):
+        call("sg_tracer_trace", self.h, _stream(stream))
+
+    def check(self, stream=None) -> int:
+        r = ctypes.c_int32()
+        call("sg_tracer_check", self.h, ctypes.byref(r), _stream(stream))
+        return r.value
+
+    def sizes(self, stream=None):
+        nl = ctypes.c_int64()
+        nv = ctypes.c_int64()
+        call("sg_tracer_get_lines", self.h, ctypes.byref(nl), ctypes.byref(nv), None, None, None, None, None,
+             _stream(stream))
+        return nl.value, nv.value
+
+    def get_lines(self, device="cuda", stream=None) -> Lines:
+        """CSR lines; device 'cuda' (the tracer's GPU) or 'pinned' (page-locked host)."""
+        nl, nv = self.sizes(stream)
+        if device == "pinned":
+            kw = dict(pin_memory=True)
+        else:
+            kw = dict(device=f"cuda:{self.ctx.device}")
+        off = torch.empty(nl + 1, dtype=torch.int64, **kw)
+        vert = torch.empty((max(nv, 1), 3), dtype=torch.float32, **kw)
+        st = torch.empty(max(nl, 1), dtype=torch.uint8, **kw)
+        mg = torch.empty(max(nl, 1), dtype=torch.float32, **kw)
+        src = torch.empty(max(nl, 1), dtype=torch.int32, **kw)
+        call("sg_tracer_get_lines", self.h, None, None, _ptr(off), _ptr(vert), _ptr(st), _ptr(mg), _ptr(src),
+             _stream(stream))
+        return Lines(off, vert[:nv], st[:nl], mg[:nl], src[:nl])
+
+    def total_steps(self, stream=None) -> int:
+        n = ctypes.c_int64()
+        call("sg_tracer_total_steps", self.h, ctypes.byref(n), _stream(stream))
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib().sg_tracer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

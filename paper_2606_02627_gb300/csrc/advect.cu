@@ -1,0 +1,546 @@
+// Streamline advection kernels.
+//
+//  * round_kernel: the persistent form.  Each warp pops particles from the
+//    brick-sorted queue of the round (warp-aggregated atomics on one cursor),
+//    advances each lane by RK4 steps inside its brick, and refills lanes whose
+//    particle stopped, left the brick or used its steps for the round
+//    (__ballot_sync / __shfl_sync).  A particle that leaves its brick is
+//    appended to the outgoing buffer, from which the binning kernels build the
+//    destination bricks' queues for the next round: the paper's emitOutgoing /
+//    particle forwarding (Sec. 3.1.2) as an exchange inside one GPU.
+//  * per_step_kernel: Listing 1 as written: one thread per particle, one RK4
+//    step per launch, every particle emitted to the queue of its destination
+//    brick (which may be its own).
+//  * per_seed_kernel: one thread per seed to termination on the global float3
+//    field; no bricks, no queues.
+//  * upload_kernel: seeds to particles; writes each line's first vertex.
+//
+// RK4 (Listing 1): k1 = dt v(P0), P1 = P0 + k1/2, k2 = dt v(P1),
+// P2 = P0 + k2/2, k3 = dt v(P2), P3 = P0 + k3, k4 = dt v(P3),
+// P' = P0 + (k1 + 2 k2 + 2 k3 + k4)/6, with v in cells per unit time.
+#include <math.h>
+
+#include "tracer.cuh"
+
+namespace sg {
+
+template <int DT>
+struct BrickRef {
+    const typename Elem<DT>::T *data;
+    float scale;
+    int lo[3];   // first owned cell per axis
+    int hi[3];   // one past the last owned cell (dims for the last brick)
+};
+
+template <int DT>
+__device__ __forceinline__ void brick_of(const DevField &F, const int c[3], BrickRef<DT> &br)
+{
+    int b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int bb = c[a] / F.n[a];
+        if (bb > F.B[a] - 1) bb = F.B[a] - 1;
+        b[a] = bb;
+        br.lo[a] = bb * F.n[a];
+        br.hi[a] = (bb == F.B[a] - 1) ? F.dims[a] : br.lo[a] + F.n[a];
+    }
+    const int id = (b[2] * F.B[1] + b[1]) * F.B[0] + b[0];
+    br.data = reinterpret_cast<const typename Elem<DT>::T *>(F.data) + (long long)id * F.brick_stride;
+    br.scale = (DT == SG_F32) ? 1.0f : __ldg(F.scales + id);
+}
+
+// Trilinear sample at global cell c, fraction f, from the particle's brick.
+// Returns SG_LINE_HALO if the point is outside the brick's ghost shell.
+template <int DT, int LAYOUT>
+__device__ __forceinline__ int sample_brick(const DevField &F, const BrickRef<DT> &br, const int c[3], const float f[3],
+                                            float3 &v)
+{
+    const int sx = c[0] - br.lo[0] + 1, sy = c[1] - br.lo[1] + 1, sz = c[2] - br.lo[2] + 1;
+    if ((unsigned)sx > (unsigned)(F.S[0] - 2) || (unsigned)sy > (unsigned)(F.S[1] - 2) ||
+        (unsigned)sz > (unsigned)(F.S[2] - 2))
+        return SG_LINE_HALO;
+    v = trilerp<DT, LAYOUT>(br.data, F, sx, sy, sz, f[0], f[1], f[2]);
+    if (DT != SG_F32) {
+        v.x *= br.scale;
+        v.y *= br.scale;
+        v.z *= br.scale;
+    }
+    return 0;
+}
+
+__device__ __forceinline__ bool in_domain(const DevField &F, const int q[3], const float g[3])
+{
+    return in_axis(q[0], g[0], F.nm1[0]) && in_axis(q[1], g[1], F.nm1[1]) && in_axis(q[2], g[2], F.nm1[2]);
+}
+
+__device__ __forceinline__ float out_dist(const DevField &F, const int q[3], const float g[3])
+{
+    return fmaxf(out_axis(q[0], g[0], F.nm1[0]), fmaxf(out_axis(q[1], g[1], F.nm1[1]), out_axis(q[2], g[2], F.nm1[2])));
+}
+
+// One RK4 step of a particle owned by brick br.  On success updates (c, f)
+// and returns SG_LINE_ACTIVE; otherwise returns the stop status and leaves the
+// particle at P0.  margin is set for EXIT and STAGNANT.
+template <int DT, int LAYOUT>
+__device__ __forceinline__ int rk4_bricked(const LineParams &P, const BrickRef<DT> &br, int c[3], float f[3],
+                                           float &margin)
+{
+    const DevField &F = P.F;
+    float3 v;
+    sample_brick<DT, LAYOUT>(F, br, c, f, v);            // P0 is owned: always inside the shell
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    if (sp < P.eps) {
+        margin = (P.eps - sp) / P.eps;
+        return SG_LINE_STAGNANT;
+    }
+    float k1[3] = {v.x * P.dtc[0], v.y * P.dtc[1], v.z * P.dtc[2]};
+    int q[3];
+    float g[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k1[a], c[a], q[a], g[a]);
+    if (!in_domain(F, q, g)) {
+        margin = out_dist(F, q, g);
+        return SG_LINE_EXIT;
+    }
+    if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    float k2[3] = {v.x * P.dtc[0], v.y * P.dtc[1], v.z * P.dtc[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k2[a], c[a], q[a], g[a]);
+    if (!in_domain(F, q, g)) {
+        margin = out_dist(F, q, g);
+        return SG_LINE_EXIT;
+    }
+    if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    float k3[3] = {v.x * P.dtc[0], v.y * P.dtc[1], v.z * P.dtc[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) locate(f[a], k3[a], c[a], q[a], g[a]);
+    if (!in_domain(F, q, g)) {
+        margin = out_dist(F, q, g);
+        return SG_LINE_EXIT;
+    }
+    if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    const float k4[3] = {v.x * P.dtc[0], v.y * P.dtc[1], v.z * P.dtc[2]};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d = (k1[a] + k4[a] + 2.0f * (k2[a] + k3[a])) * (1.0f / 6.0f);
+        locate(f[a], d, c[a], q[a], g[a]);
+    }
+    if (!in_domain(F, q, g)) {
+        margin = out_dist(F, q, g);
+        return SG_LINE_EXIT;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c[a] = q[a];
+        f[a] = g[a];
+    }
+    return SG_LINE_ACTIVE;
+}
+
+__device__ __forceinline__ void write_vertex(const LineParams &P, uint32_t line, uint32_t step, const int c[3],
+                                             const float f[3])
+{
+    float *o = P.slab + ((long long)line * P.W + step) * 3;
+    o[0] = fmaf(P.F.spacing[0], (float)c[0] + f[0], P.F.origin[0]);
+    o[1] = fmaf(P.F.spacing[1], (float)c[1] + f[1], P.F.origin[1]);
+    o[2] = fmaf(P.F.spacing[2], (float)c[2] + f[2], P.F.origin[2]);
+}
+
+__device__ __forceinline__ uint8_t stop_code(const LineParams &P, int st, float margin)
+{
+    uint8_t s = (uint8_t)st;
+    if ((st == SG_LINE_EXIT && margin < P.tie_cells) || (st == SG_LINE_STAGNANT && margin < P.tie_eps_rel))
+        s |= SG_LINE_TIE;
+    return s;
+}
+
+__device__ __forceinline__ void store_particle(Particle *dst, const int c[3], const float f[3], uint32_t line,
+                                               uint32_t step)
+{
+    float4 a = make_float4(f[0], f[1], f[2], __uint_as_float(line));
+    int4 b = make_int4(c[0], c[1], c[2], (int)step);
+    reinterpret_cast<float4 *>(dst)[0] = a;
+    reinterpret_cast<int4 *>(dst)[1] = b;
+}
+
+__device__ __forceinline__ void load_particle(const Particle *src, int c[3], float f[3], uint32_t &line, uint32_t &step)
+{
+    const float4 a = reinterpret_cast<const float4 *>(src)[0];
+    const int4 b = reinterpret_cast<const int4 *>(src)[1];
+    f[0] = a.x;
+    f[1] = a.y;
+    f[2] = a.z;
+    line = __float_as_uint(a.w);
+    c[0] = b.x;
+    c[1] = b.y;
+    c[2] = b.z;
+    step = (uint32_t)b.w;
+}
+
+// Warp-aggregated append: every lane of the warp calls it; lanes with `want`
+// get consecutive slots of dst from one atomicAdd on *count.
+__device__ __forceinline__ void warp_append(bool want, Particle *dst, uint32_t *count, const int c[3], const float f[3],
+                                            uint32_t line, uint32_t step)
+{
+    const unsigned m = __ballot_sync(SG_FULL_MASK, want);
+    if (!m) return;
+    const unsigned lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(count, (uint32_t)__popc(m));
+    base = __shfl_sync(SG_FULL_MASK, base, leader);
+    if (want) store_particle(dst + base + __popc(m & ((1u << lane) - 1u)), c, f, line, step);
+}
+
+// ------------------------------------------------------------------ persistent round kernel
+
+template <int DT, int LAYOUT>
+__global__ void __launch_bounds__(256) round_kernel(const __grid_constant__ LineParams P)
+{
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t q_count = P.ctrl->q_count;
+    const uint32_t horizon = P.ctrl->horizon;
+    bool active = false;
+    bool drained = q_count == 0;
+    int c[3] = {0, 0, 0};
+    float f[3] = {0.f, 0.f, 0.f};
+    uint32_t line = 0, step = 0, here = 0;
+    BrickRef<DT> br;
+    br.data = nullptr;
+    br.scale = 1.0f;
+    for (int a = 0; a < 3; ++a) br.lo[a] = br.hi[a] = 0;
+
+    while (true) {
+        const unsigned need = __ballot_sync(SG_FULL_MASK, !active);
+        if (need && !drained) {
+            const int leader = __ffs(need) - 1;
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(&P.ctrl->q_head, (uint32_t)__popc(need));
+            base = __shfl_sync(SG_FULL_MASK, base, leader);
+            if (base + (uint32_t)__popc(need) >= q_count) drained = true;
+            if (!active) {
+                const uint32_t my = base + __popc(need & lt);
+                if (my < q_count) {
+                    load_particle(P.q + my, c, f, line, step);
+                    brick_of<DT>(P.F, c, br);
+                    active = true;
+                    here = 0;
+                }
+            }
+        }
+        if (__ballot_sync(SG_FULL_MASK, active) == 0) break;
+
+        int ev = EV_NONE, st = SG_LINE_ACTIVE;
+        float margin = INFINITY;
+        if (active) {
+            if (step >= horizon) {
+                if (step >= P.max_steps) {
+                    ev = EV_STOP;
+                    st = SG_LINE_MAXSTEPS;
+                } else {
+                    ev = EV_PARK;
+                }
+            } else if (here >= P.steps_per_round) {
+                ev = EV_APPEND;
+            } else {
+                st = rk4_bricked<DT, LAYOUT>(P, br, c, f, margin);
+                if (st != SG_LINE_ACTIVE) {
+                    ev = EV_STOP;
+                } else {
+                    ++step;
+                    ++here;
+                    write_vertex(P, line, step, c, f);
+                    if (step >= horizon) {
+                        if (step >= P.max_steps) {
+                            ev = EV_STOP;
+                            st = SG_LINE_MAXSTEPS;
+                        } else {
+                            ev = EV_PARK;
+                        }
+                    } else if (c[0] < br.lo[0] || c[0] >= br.hi[0] || c[1] < br.lo[1] || c[1] >= br.hi[1] ||
+                               c[2] < br.lo[2] || c[2] >= br.hi[2]) {
+                        ev = EV_APPEND;       // destinationID(new position) != this brick
+                    }
+                }
+            }
+        }
+        warp_append(ev == EV_APPEND, P.o, &P.ctrl->o_count, c, f, line, step);
+        warp_append(ev == EV_PARK, P.park, &P.ctrl->p_count, c, f, line, step);
+        if (ev == EV_STOP) {
+            P.line_len[line] = step + 1;
+            P.line_status[line] = stop_code(P, st, margin);
+            P.line_margin[line] = margin;
+        } else if (ev == EV_PARK) {
+            P.line_len[line] = step + 1;
+        }
+        if (ev != EV_NONE) active = false;
+    }
+}
+
+// ------------------------------------------------------------------ Listing 1: one launch per step
+
+template <int DT, int LAYOUT>
+__global__ void __launch_bounds__(256) per_step_kernel(const __grid_constant__ LineParams P)
+{
+    const uint32_t q_count = P.ctrl->q_count;
+    const uint32_t horizon = P.ctrl->horizon;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // warp-uniform trip count: each warp takes 32 consecutive particles per pass
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < q_count; base += stride) {
+        const uint32_t idx = base + (threadIdx.x & 31);
+        const bool valid = idx < q_count;
+        int c[3] = {0, 0, 0};
+        float f[3] = {0.f, 0.f, 0.f};
+        uint32_t line = 0, step = 0;
+        int ev = EV_NONE, st = SG_LINE_ACTIVE;
+        float margin = INFINITY;
+        if (valid) {
+            load_particle(P.q + idx, c, f, line, step);       // getIncoming(particleID)
+            if (step >= horizon) {
+                if (step >= P.max_steps) {
+                    ev = EV_STOP;
+                    st = SG_LINE_MAXSTEPS;
+                } else {
+                    ev = EV_PARK;
+                }
+            } else {
+                BrickRef<DT> br;
+                brick_of<DT>(P.F, c, br);
+                st = rk4_bricked<DT, LAYOUT>(P, br, c, f, margin);
+                if (st != SG_LINE_ACTIVE) {
+                    ev = EV_STOP;
+                } else {
+                    ++step;
+                    write_vertex(P, line, step, c, f);
+                    if (step >= P.max_steps) {
+                        ev = EV_STOP;
+                        st = SG_LINE_MAXSTEPS;
+                    } else {
+                        ev = (step >= horizon) ? EV_PARK : EV_APPEND;   // emitOutgoing(p, destinationID(P'))
+                    }
+                }
+            }
+        }
+        warp_append(ev == EV_APPEND, P.o, &P.ctrl->o_count, c, f, line, step);
+        warp_append(ev == EV_PARK, P.park, &P.ctrl->p_count, c, f, line, step);
+        if (ev == EV_STOP) {
+            P.line_len[line] = step + 1;
+            P.line_status[line] = stop_code(P, st, margin);
+            P.line_margin[line] = margin;
+        } else if (ev == EV_PARK) {
+            P.line_len[line] = step + 1;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ per-seed kernel (global float3 field)
+
+// Trilinear sample of the global float3 AoS array at index point p (inside
+// the domain); the lower cell index is clamped to dims-2.
+__device__ __forceinline__ float3 sample_global(const float *__restrict__ Fg, const DevField &F, float px, float py,
+                                                float pz)
+{
+    int cx = min((int)floorf(px), F.nm1[0] - 1);
+    int cy = min((int)floorf(py), F.nm1[1] - 1);
+    int cz = min((int)floorf(pz), F.nm1[2] - 1);
+    const float fx = px - (float)cx, fy = py - (float)cy, fz = pz - (float)cz;
+    const long long sx = 3, sy = 3ll * F.dims[0], sz = 3ll * F.dims[0] * F.dims[1];
+    const float *b = Fg + (long long)cz * sz + (long long)cy * sy + (long long)cx * sx;
+    float3 r;
+    float v[8];
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            v[k] = __ldg(b + comp + ((k & 1) ? sx : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
+        const float val = lerpf(lerpf(lerpf(v[0], v[1], fx), lerpf(v[2], v[3], fx), fy),
+                                lerpf(lerpf(v[4], v[5], fx), lerpf(v[6], v[7], fx), fy), fz);
+        if (comp == 0) r.x = val;
+        else if (comp == 1) r.y = val;
+        else r.z = val;
+    }
+    return r;
+}
+
+__device__ __forceinline__ bool in_box(const DevField &F, float x, float y, float z)
+{
+    return x >= 0.f && x <= (float)F.nm1[0] && y >= 0.f && y <= (float)F.nm1[1] && z >= 0.f && z <= (float)F.nm1[2];
+}
+
+__device__ __forceinline__ float box_out(const DevField &F, float x, float y, float z)
+{
+    float d = 0.f;
+    d = fmaxf(d, -x);
+    d = fmaxf(d, x - (float)F.nm1[0]);
+    d = fmaxf(d, -y);
+    d = fmaxf(d, y - (float)F.nm1[1]);
+    d = fmaxf(d, -z);
+    d = fmaxf(d, z - (float)F.nm1[2]);
+    return d;
+}
+
+__global__ void __launch_bounds__(256) per_seed_kernel(const __grid_constant__ LineParams P)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n_lines) return;
+    const float *Fg = reinterpret_cast<const float *>(P.F.data);
+    const DevField &F = P.F;
+    // index-space seed, converted in double precision
+    const double sx = ((double)P.seeds[3 * i] - P.origin_d[0]) / P.spacing_d[0];
+    const double sy = ((double)P.seeds[3 * i + 1] - P.origin_d[1]) / P.spacing_d[1];
+    const double sz = ((double)P.seeds[3 * i + 2] - P.origin_d[2]) / P.spacing_d[2];
+    if (!(sx >= 0.0 && sx <= F.nm1[0] && sy >= 0.0 && sy <= F.nm1[1] && sz >= 0.0 && sz <= F.nm1[2])) {
+        P.line_len[i] = 0;
+        P.line_status[i] = SG_LINE_OUT;
+        P.line_margin[i] = INFINITY;
+        return;
+    }
+    float px = (float)sx, py = (float)sy, pz = (float)sz;
+    float *out = P.slab + (long long)i * P.W * 3;
+    out[0] = P.seeds[3 * i];
+    out[1] = P.seeds[3 * i + 1];
+    out[2] = P.seeds[3 * i + 2];
+    uint32_t step = 0;
+    int st = SG_LINE_MAXSTEPS;
+    float margin = INFINITY;
+    while (step < P.max_steps) {
+        float3 v = sample_global(Fg, F, px, py, pz);
+        if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
+        const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+        if (sp < P.eps) { st = SG_LINE_STAGNANT; margin = (P.eps - sp) / P.eps; break; }
+        const float k1x = v.x * P.dtc[0], k1y = v.y * P.dtc[1], k1z = v.z * P.dtc[2];
+        float qx = px + 0.5f * k1x, qy = py + 0.5f * k1y, qz = pz + 0.5f * k1z;
+        if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
+        v = sample_global(Fg, F, qx, qy, qz);
+        if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
+        const float k2x = v.x * P.dtc[0], k2y = v.y * P.dtc[1], k2z = v.z * P.dtc[2];
+        qx = px + 0.5f * k2x; qy = py + 0.5f * k2y; qz = pz + 0.5f * k2z;
+        if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
+        v = sample_global(Fg, F, qx, qy, qz);
+        if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
+        const float k3x = v.x * P.dtc[0], k3y = v.y * P.dtc[1], k3z = v.z * P.dtc[2];
+        qx = px + k3x; qy = py + k3y; qz = pz + k3z;
+        if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
+        v = sample_global(Fg, F, qx, qy, qz);
+        if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
+        const float k4x = v.x * P.dtc[0], k4y = v.y * P.dtc[1], k4z = v.z * P.dtc[2];
+        qx = px + (k1x + k4x + 2.0f * (k2x + k3x)) * (1.0f / 6.0f);
+        qy = py + (k1y + k4y + 2.0f * (k2y + k3y)) * (1.0f / 6.0f);
+        qz = pz + (k1z + k4z + 2.0f * (k2z + k3z)) * (1.0f / 6.0f);
+        if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
+        px = qx; py = qy; pz = qz;
+        ++step;
+        float *o = out + 3ll * step;
+        o[0] = fmaf(F.spacing[0], px, F.origin[0]);
+        o[1] = fmaf(F.spacing[1], py, F.origin[1]);
+        o[2] = fmaf(F.spacing[2], pz, F.origin[2]);
+    }
+    P.line_len[i] = step + 1;
+    P.line_status[i] = stop_code(P, st, margin);
+    P.line_margin[i] = margin;
+}
+
+// ------------------------------------------------------------------ seed upload
+
+__global__ void upload_kernel(const __grid_constant__ LineParams P)
+{
+    const long long n = P.n_lines;
+    const unsigned lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
+        const long long i = base + lane;
+        bool keep = false;
+        int c[3] = {0, 0, 0};
+        float f[3] = {0.f, 0.f, 0.f};
+        if (i < n) {
+            double p[3];
+            bool inside = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                p[a] = ((double)P.seeds[3 * i + a] - P.origin_d[a]) / P.spacing_d[a];
+                inside = inside && (p[a] >= 0.0 && p[a] <= (double)P.F.nm1[a]);
+            }
+            if (!inside) {
+                P.line_len[i] = 0;
+                P.line_status[i] = SG_LINE_OUT;
+                P.line_margin[i] = INFINITY;
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const double fl = floor(p[a]);
+                    c[a] = (int)fl;
+                    f[a] = (float)(p[a] - fl);
+                    if (f[a] >= 1.0f) {
+                        f[a] = 0.0f;
+                        c[a] += 1;
+                    }
+                }
+                float *o = P.slab + (long long)i * P.W * 3;
+                o[0] = P.seeds[3 * i];
+                o[1] = P.seeds[3 * i + 1];
+                o[2] = P.seeds[3 * i + 2];
+                P.line_len[i] = 1;
+                P.line_status[i] = SG_LINE_ACTIVE;
+                P.line_margin[i] = INFINITY;
+                keep = true;
+            }
+        }
+        warp_append(keep, P.park, &P.ctrl->p_count, c, f, (uint32_t)i, 0u);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+sg_status launch_upload(sg_tracer *t, cudaStream_t s)
+{
+    LineParams P = line_params(t);
+    if (t->p.kernel == SG_KERNEL_PER_SEED) return SG_OK;   // the per-seed kernel reads the seeds itself
+    int grid = (int)((t->n_seeds + 255) / 256);
+    if (grid > t->ctx->sm_count * 16) grid = t->ctx->sm_count * 16;
+    if (grid < 1) grid = 1;
+    upload_kernel<<<grid, 256, 0, s>>>(P);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+sg_status launch_per_seed(sg_tracer *t, cudaStream_t s)
+{
+    LineParams P = line_params(t);
+    if (t->n_seeds == 0) return SG_OK;
+    const int block = t->block > 0 ? t->block : 256;
+    per_seed_kernel<<<(unsigned)((t->n_seeds + block - 1) / block), block, 0, s>>>(P);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+template <int DT, int LAYOUT>
+static void launch_round_t(const LineParams &P, int grid, int block, int kernel, cudaStream_t s)
+{
+    if (kernel == SG_KERNEL_PER_STEP) per_step_kernel<DT, LAYOUT><<<grid, block, 0, s>>>(P);
+    else round_kernel<DT, LAYOUT><<<grid, block, 0, s>>>(P);
+}
+
+sg_status launch_round(sg_tracer *t, cudaStream_t s)
+{
+    LineParams P = line_params(t);
+    const int dt = t->field->desc.dtype, lay = t->field->desc.layout;
+    const int k = t->p.kernel;
+    if (lay == SG_LAYOUT_LINEAR) {
+        if (dt == SG_F32) launch_round_t<SG_F32, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);
+        else if (dt == SG_BF16) launch_round_t<SG_BF16, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);
+        else launch_round_t<SG_F16, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);
+    } else {
+        if (dt == SG_F32) launch_round_t<SG_F32, SG_LAYOUT_TILED4>(P, t->grid, t->block, k, s);
+        else if (dt == SG_BF16) launch_round_t<SG_BF16, SG_LAYOUT_TILED4>(P, t->grid, t->block, k, s);
+        else launch_round_t<SG_F16, SG_LAYOUT_TILED4>(P, t->grid, t->block, k, s);
+    }
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+}  // namespace sg

@@ -1,0 +1,276 @@
+// Internal definitions shared by the translation units of libstreamgb.
+//
+// Method (Zellmann et al., "Streami", Sec. 3.1, Listing 1): particles are
+// advected by classical RK4 with stage points P0 + k1/2, P0 + k2/2, P0 + k3,
+// k_i = dt * v(stage point) / spacing (cells), through a structured field
+// sampled by trilinear interpolation; a failed sample ends the particle; the
+// destination macrocell (brick) is computed from the new position.
+//
+// Position representation: a particle keeps its global cell index (int) and
+// its fraction inside the cell (float in [0,1)).  Stage points are formed as
+// fraction + offset relative to the particle's cell, so the fraction used by
+// the interpolation carries ~2^-24 cells of rounding wherever the particle is,
+// and moving between bricks needs no change of coordinates.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "streamgb.h"
+
+#define SG_FULL_MASK 0xffffffffu
+
+namespace sg {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+sg_status cuda_error(cudaError_t e, const char *what);
+#define SG_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::sg::cuda_error(e_, #call);      \
+    } while (0)
+#define SG_CHECK(cond, code, ...)                                       \
+    do {                                                                \
+        if (!(cond)) {                                                  \
+            ::sg::set_error(__VA_ARGS__);                               \
+            return (code);                                              \
+        }                                                               \
+    } while (0)
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over a caller-owned buffer.
+struct Carve {
+    char *base;
+    size_t off;
+    size_t cap;
+    void *take(size_t bytes, size_t align = 256) {
+        off = align_up(off, align);
+        void *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+// ------------------------------------------------------------------ field geometry
+
+// Device view of one resident slot of a bricked field.
+struct DevField {
+    const char *data;        // slot storage: nb bricks of brick_bytes each
+    const float *scales;     // per-brick decode scale (1 for FP32)
+    int dims[3];             // samples per axis
+    int nm1[3];              // dims - 1: upper face index
+    int n[3];                // owned cells per brick per axis
+    int B[3];                // bricks per axis
+    int S[3];                // stored samples per brick per axis (n + 3)
+    int T[3];                // tiles of 4 per axis (tiled layout)
+    long long brick_elems;   // samples per brick (with tile padding)
+    long long brick_stride;  // samples from one brick's start to the next
+    float origin[3];
+    float spacing[3];
+};
+
+}  // namespace sg
+
+struct sg_context {
+    int device;
+    int sm_count;
+    int max_threads_per_sm;
+    int max_smem_optin;
+    long long l2_bytes;
+};
+
+struct sg_field {
+    sg_context *ctx;
+    sg_field_desc desc;
+    sg::DevField geom;       // data/scales of slot 0 (per-slot pointers below)
+    char *storage;
+    size_t bytes;
+    int nb;
+    size_t elem_bytes;       // 16 (FP32) or 8 (BF16/FP16); 12 for SG_FIELD_GLOBAL
+    size_t brick_bytes;
+    char *slot_data[64];
+    float *slot_scales[64];
+    unsigned *maxbits;       // nb scratch words for the per-brick max-abs reduction
+    float *staging;          // one global FP32 slice (streamed slices)
+    unsigned *speed_bits;    // 1 word: max speed reduction
+    int slot_slice[64];      // slice held by each slot (-1 = none)
+    cudaEvent_t slot_ready[64];  // recorded when a slot's contents are complete
+    cudaEvent_t slot_used[64];   // recorded after the last queued step that reads a slot
+};
+
+namespace sg {
+
+DevField field_view(const sg_field *f, int slot);
+
+// ------------------------------------------------------------------ particles
+
+// Queue record of one particle: 32 bytes, two 16-byte vectors.
+struct __align__(16) Particle {
+    float fx, fy, fz;        // fraction in the cell, [0,1)
+    uint32_t line;           // line (seed) index
+    int cx, cy, cz;          // global cell index
+    uint32_t step;           // successful steps so far
+};
+
+// Counters of a tracer's round loop (device memory).
+struct Ctrl {
+    uint32_t q_count;        // particles in the brick-sorted queue of this round
+    uint32_t q_head;         // pop cursor of that queue
+    uint32_t o_count;        // records appended to the outgoing buffer this round
+    uint32_t p_count;        // parked records (reached the step horizon)
+    uint32_t round;          // rounds run by the current call
+    uint32_t err;            // bit 0: round cap reached with particles left
+    uint32_t max_rounds;
+    uint32_t horizon;        // a particle advances while step < horizon
+    uint32_t last_rounds;    // rounds of the last finished call
+    uint32_t pad[7];
+};
+
+enum { CTRL_ERR_ROUND_LIMIT = 1u };
+
+// ------------------------------------------------------------------ sampling helpers
+
+template <int DT> struct Elem;
+template <> struct Elem<SG_F32> { using T = float4; };
+template <> struct Elem<SG_BF16> { using T = uint2; };
+template <> struct Elem<SG_F16> { using T = uint2; };
+
+template <int DT>
+__device__ __forceinline__ float3 decode_elem(typename Elem<DT>::T v);
+
+template <>
+__device__ __forceinline__ float3 decode_elem<SG_F32>(float4 v) { return make_float3(v.x, v.y, v.z); }
+
+template <>
+__device__ __forceinline__ float3 decode_elem<SG_BF16>(uint2 v)
+{
+    return make_float3(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u), __uint_as_float(v.y << 16));
+}
+
+template <>
+__device__ __forceinline__ float3 decode_elem<SG_F16>(uint2 v)
+{
+    __half2 h = *reinterpret_cast<__half2 *>(&v.x);
+    float2 a = __half22float2(h);
+    float z = __half2float(__ushort_as_half((unsigned short)(v.y & 0xffffu)));
+    return make_float3(a.x, a.y, z);
+}
+
+template <int DT>
+__device__ __forceinline__ typename Elem<DT>::T load_elem(const typename Elem<DT>::T *p)
+{
+    return __ldg(p);
+}
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+// Storage offset of a sample inside a brick (fits in 32 bits: checked when the
+// field is created), separable per axis: off = ox(x) + oy(y) + oz(z).
+template <int LAYOUT>
+struct Offsets {
+    __device__ __forceinline__ static int ox(int x, const DevField &F)
+    {
+        if (LAYOUT == SG_LAYOUT_LINEAR) return x;
+        return (x >> 2) * 64 + (x & 3);
+    }
+    __device__ __forceinline__ static int oy(int y, const DevField &F)
+    {
+        if (LAYOUT == SG_LAYOUT_LINEAR) return y * F.S[0];
+        return (y >> 2) * F.T[0] * 64 + (y & 3) * 4;
+    }
+    __device__ __forceinline__ static int oz(int z, const DevField &F)
+    {
+        if (LAYOUT == SG_LAYOUT_LINEAR) return z * F.S[0] * F.S[1];
+        return (z >> 2) * F.T[0] * F.T[1] * 64 + (z & 3) * 16;
+    }
+};
+
+inline __host__ __device__ long long storage_index(int layout, int x, int y, int z, const DevField &F)
+{
+    if (layout == SG_LAYOUT_LINEAR) return ((long long)z * F.S[1] + y) * F.S[0] + x;
+    return (((long long)(z >> 2) * F.T[1] + (y >> 2)) * F.T[0] + (x >> 2)) * 64 + ((z & 3) * 4 + (y & 3)) * 4 + (x & 3);
+}
+
+// Trilinear interpolation inside one brick: (sx, sy, sz) is the storage index
+// of the lower corner, (fx, fy, fz) the fractions.  Returns the undecoded-scale
+// value (multiply by the brick scale for world units).
+template <int DT, int LAYOUT>
+__device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict__ brick, const DevField &F,
+                                          int sx, int sy, int sz, float fx, float fy, float fz)
+{
+    using O = Offsets<LAYOUT>;
+    const int x0 = O::ox(sx, F), x1 = O::ox(sx + 1, F);
+    const int y0 = O::oy(sy, F), y1 = O::oy(sy + 1, F);
+    const int z0 = O::oz(sz, F), z1 = O::oz(sz + 1, F);
+    const auto e000 = load_elem<DT>(brick + (z0 + y0 + x0));
+    const auto e100 = load_elem<DT>(brick + (z0 + y0 + x1));
+    const auto e010 = load_elem<DT>(brick + (z0 + y1 + x0));
+    const auto e110 = load_elem<DT>(brick + (z0 + y1 + x1));
+    const auto e001 = load_elem<DT>(brick + (z1 + y0 + x0));
+    const auto e101 = load_elem<DT>(brick + (z1 + y0 + x1));
+    const auto e011 = load_elem<DT>(brick + (z1 + y1 + x0));
+    const auto e111 = load_elem<DT>(brick + (z1 + y1 + x1));
+    const float3 c000 = decode_elem<DT>(e000), c100 = decode_elem<DT>(e100);
+    const float3 c010 = decode_elem<DT>(e010), c110 = decode_elem<DT>(e110);
+    const float3 c001 = decode_elem<DT>(e001), c101 = decode_elem<DT>(e101);
+    const float3 c011 = decode_elem<DT>(e011), c111 = decode_elem<DT>(e111);
+    float3 r;
+    r.x = lerpf(lerpf(lerpf(c000.x, c100.x, fx), lerpf(c010.x, c110.x, fx), fy),
+                lerpf(lerpf(c001.x, c101.x, fx), lerpf(c011.x, c111.x, fx), fy), fz);
+    r.y = lerpf(lerpf(lerpf(c000.y, c100.y, fx), lerpf(c010.y, c110.y, fx), fy),
+                lerpf(lerpf(c001.y, c101.y, fx), lerpf(c011.y, c111.y, fx), fy), fz);
+    r.z = lerpf(lerpf(lerpf(c000.z, c100.z, fx), lerpf(c010.z, c110.z, fx), fy),
+                lerpf(lerpf(c001.z, c101.z, fx), lerpf(c011.z, c111.z, fx), fy), fz);
+    return r;
+}
+
+// Not finite in any component (NaN or inf).  The sum of magnitudes is finite
+// exactly when every component is finite, for |v| well below FLT_MAX.
+__device__ __forceinline__ bool bad3(float3 v) { return !(fabsf(v.x) + fabsf(v.y) + fabsf(v.z) < INFINITY); }
+
+// Stage point relative to a particle's cell: q = frac + dk gives the cell
+// offset floor(q) and the new fraction q - floor(q) (exact for |q| < 2^23);
+// a fraction that rounds up to 1 moves to the next cell.
+__device__ __forceinline__ void locate(float frac, float dk, int cell, int &cell_out, float &frac_out)
+{
+    const float q = frac + dk;
+    const float d = floorf(q);
+    float fr = q - d;
+    int di = (int)d;
+    if (fr >= 1.0f) {
+        fr = 0.0f;
+        di += 1;
+    }
+    cell_out = cell + di;
+    frac_out = fr;
+}
+
+// Inside the closed domain [0, N-1] along one axis.
+__device__ __forceinline__ bool in_axis(int cell, float frac, int nm1)
+{
+    return cell >= 0 && (cell < nm1 || (cell == nm1 && frac == 0.0f));
+}
+
+// Distance outside the domain along one axis (0 if inside).
+__device__ __forceinline__ float out_axis(int cell, float frac, int nm1)
+{
+    if (cell < 0) return (float)(-cell) - frac;
+    if (cell > nm1 || (cell == nm1 && frac > 0.0f)) return (float)(cell - nm1) + frac;
+    return 0.0f;
+}
+
+// ------------------------------------------------------------------ host-side launchers (per file)
+
+sg_status launch_brick_store(sg_field *f, int slot, const float *src, int src_mode, int brick_index,
+                             cudaStream_t s);
+sg_status launch_max_speed(sg_field *f, int slot, cudaStream_t s);
+
+int pointer_kind(const void *p);   // 0 = device/managed, 1 = page-locked host, 2 = pageable host, -1 error
+enum { PTR_DEVICE = 0, PTR_PINNED = 1, PTR_PAGEABLE = 2 };
+
+}  // namespace sg

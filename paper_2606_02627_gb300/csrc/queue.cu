@@ -1,0 +1,200 @@
+// Per-brick particle queues: the exchange step between rounds.
+//
+// The paper forwards particles between GPUs with RaFI: emitOutgoing() buffers
+// a particle for its destination rank and a collective all-to-all moves the
+// buffers; the host learns whether any particle is left anywhere
+// (Sec. 3.1.2, Listing 2).  Here every brick lives on the same GPU, so the
+// exchange is a counting sort of the outgoing records by destination brick
+// (histogram, exclusive scan, scatter) into the next round's queue, and the
+// "any particle left" reduction is the queue length, which a device-side
+// control kernel turns into the condition of the CUDA graph's while-node.
+#include "tracer.cuh"
+
+namespace sg {
+
+struct BinArgs {
+    const Particle *src;
+    uint32_t *src_count;
+    Particle *dst;
+    uint32_t *brick_count;
+    uint32_t *brick_cursor;
+    Ctrl *ctrl;
+    int n[3];
+    int B[3];
+    int nb;
+};
+
+__device__ __forceinline__ int brick_id(const BinArgs &A, int cx, int cy, int cz)
+{
+    const int bx = min(cx / A.n[0], A.B[0] - 1);
+    const int by = min(cy / A.n[1], A.B[1] - 1);
+    const int bz = min(cz / A.n[2], A.B[2] - 1);
+    return (bz * A.B[1] + by) * A.B[0] + bx;
+}
+
+// Histogram of destination bricks (shared-memory counters when they fit).
+__global__ void bin_count_kernel(BinArgs A)
+{
+    extern __shared__ uint32_t hist[];
+    const bool local = A.nb <= 8192;
+    if (local)
+        for (int b = threadIdx.x; b < A.nb; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const uint32_t n = *A.src_count;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 c = reinterpret_cast<const int4 *>(A.src + i)[1];
+        const int b = brick_id(A, c.x, c.y, c.z);
+        if (local) atomicAdd(hist + b, 1u);
+        else atomicAdd(A.brick_count + b, 1u);
+    }
+    __syncthreads();
+    if (local)
+        for (int b = threadIdx.x; b < A.nb; b += blockDim.x)
+            if (hist[b]) atomicAdd(A.brick_count + b, hist[b]);
+}
+
+// Exclusive scan of the brick histogram (one block): queue offsets per brick,
+// the round's queue length; clears the histogram for the next use.
+__global__ void bin_scan_kernel(BinArgs A)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < A.nb; base += blockDim.x) {
+        const int b = base + threadIdx.x;
+        const uint32_t v = b < A.nb ? A.brick_count[b] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(SG_FULL_MASK, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < (blockDim.x >> 5) ? warp_sums[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(SG_FULL_MASK, w, o);
+                if ((int)lane >= o) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t before = carry + (warp ? warp_sums[warp - 1] : 0u) + x - v;
+        if (b < A.nb) {
+            A.brick_cursor[b] = before;
+            A.brick_count[b] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) A.ctrl->q_count = carry;
+}
+
+// Scatter each record to its brick's segment; lanes with the same brick share
+// one atomicAdd (__match_any_sync).
+__global__ void bin_scatter_kernel(BinArgs A)
+{
+    const uint32_t n = *A.src_count;
+    const unsigned lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < n; base += stride) {
+        const uint32_t i = base + lane;
+        const bool valid = i < n;
+        const unsigned vm = __ballot_sync(SG_FULL_MASK, valid);
+        if (!valid) continue;
+        const int4 *s = reinterpret_cast<const int4 *>(A.src + i);
+        const int4 r0 = s[0], r1 = s[1];
+        const int b = brick_id(A, r1.x, r1.y, r1.z);
+        const unsigned peers = __match_any_sync(vm, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t pos = 0;
+        if ((int)lane == leader) pos = atomicAdd(A.brick_cursor + b, (uint32_t)__popc(peers));
+        pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1u));
+        int4 *d = reinterpret_cast<int4 *>(A.dst + pos);
+        d[0] = r0;
+        d[1] = r1;
+    }
+}
+
+// After a scatter: the source buffer is empty, the queue cursor rewinds, and
+// the loop continues while the queue holds particles and the round cap is not
+// reached.  mode 0: after binning the parked records (start of a call);
+// mode 1: after binning a round's outgoing records.
+__global__ void ctrl_kernel(Ctrl *ctrl, uint32_t *src_count, int mode, cudaGraphConditionalHandle h, int use_graph)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *src_count = 0;
+    ctrl->q_head = 0;
+    if (mode == 1) ctrl->round += 1;
+    const bool more = ctrl->q_count > 0;
+    const bool capped = ctrl->round >= ctrl->max_rounds;
+    if (more && capped) ctrl->err |= CTRL_ERR_ROUND_LIMIT;
+    if (!more || capped) ctrl->last_rounds = ctrl->round;
+    if (use_graph) cudaGraphSetConditional(h, (more && !capped) ? 1u : 0u);
+}
+
+__global__ void prepare_kernel(Ctrl *ctrl, uint32_t horizon, uint32_t max_rounds)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    ctrl->q_count = 0;
+    ctrl->q_head = 0;
+    ctrl->o_count = 0;
+    ctrl->round = 0;
+    ctrl->err = 0;
+    ctrl->horizon = horizon;
+    ctrl->max_rounds = max_rounds;
+}
+
+sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s)
+{
+    prepare_kernel<<<1, 32, 0, s>>>(t->ctrl, horizon, max_rounds);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+// mode 0: bin parked records (start of a call); mode 1: bin outgoing records.
+sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStream_t s, bool in_graph,
+                     unsigned long long cond_handle, int mode)
+{
+    BinArgs A;
+    A.src = src;
+    A.src_count = src_count;
+    A.dst = t->q;
+    A.brick_count = t->brick_count;
+    A.brick_cursor = t->brick_cursor;
+    A.ctrl = t->ctrl;
+    for (int a = 0; a < 3; ++a) {
+        A.n[a] = t->field->geom.n[a];
+        A.B[a] = t->field->geom.B[a];
+    }
+    A.nb = t->nb;
+    const int grid = t->ctx->sm_count * 2;
+    const size_t smem = A.nb <= 8192 ? sizeof(uint32_t) * A.nb : 0;
+    bin_count_kernel<<<grid, 512, smem, s>>>(A);
+    SG_CUDA(cudaGetLastError());
+    bin_scan_kernel<<<1, 1024, 0, s>>>(A);
+    SG_CUDA(cudaGetLastError());
+    bin_scatter_kernel<<<grid, 512, 0, s>>>(A);
+    SG_CUDA(cudaGetLastError());
+    ctrl_kernel<<<1, 32, 0, s>>>(t->ctrl, src_count, mode, (cudaGraphConditionalHandle)cond_handle, in_graph ? 1 : 0);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+__global__ void iota_kernel(int32_t *dst, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (int32_t)i;
+}
+
+sg_status launch_iota(int32_t *dst, int64_t n, cudaStream_t s)
+{
+    iota_kernel<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(dst, n);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+}  // namespace sg

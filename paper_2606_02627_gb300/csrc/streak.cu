@@ -1,0 +1,434 @@
+// Streaklines (Sec. 3.2, Listing 2): every step advances all released
+// particles through the time-dependent field, then releases one new particle
+// at every release point; a streakline joins the particles of one release
+// point in birth order.
+//
+// The field is linear in time between stored slices (time s * slice_dt): a
+// time t lies in the interval (s, s+1] in slice units, s = ceil(t/slice_dt)-1
+// (at least 0), with weight alpha = t/slice_dt - s on slice s+1.  The slices a
+// step needs are resident slots of the field, streamed in from page-locked
+// host memory on a side stream; the step waits on the slots' events.
+#include <math.h>
+#include <string.h>
+
+#include "tracer.cuh"
+
+namespace sg {
+
+struct StreakParams {
+    DevField F;                 // geometry (data pointers below)
+    const char *slot_data[6];   // per stage: slice a, slice b (3 stages)
+    const float *slot_scale[6];
+    float alpha[3];             // weight on slice b per stage time
+    Particle *state;            // [R][inj]
+    uint8_t *status;
+    float *margin;
+    const float *release;       // R x 3 world
+    long long R;
+    int inj;
+    int births;                 // particles per release point released so far
+    float dtc[3];
+    float eps;
+    double origin_d[3], spacing_d[3];
+};
+
+template <int DT>
+__device__ __forceinline__ float3 sample_slot(const DevField &F, const char *data, const float *scales, int layout,
+                                              const int q[3], const float g[3])
+{
+    using T = typename Elem<DT>::T;
+    int b[3], lo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        b[a] = min(q[a] / F.n[a], F.B[a] - 1);
+        lo[a] = b[a] * F.n[a];
+    }
+    const int id = (b[2] * F.B[1] + b[1]) * F.B[0] + b[0];
+    const T *brick = reinterpret_cast<const T *>(data) + (long long)id * F.brick_stride;
+    const int sx = q[0] - lo[0] + 1, sy = q[1] - lo[1] + 1, sz = q[2] - lo[2] + 1;
+    float3 v = layout == SG_LAYOUT_LINEAR ? trilerp<DT, SG_LAYOUT_LINEAR>(brick, F, sx, sy, sz, g[0], g[1], g[2])
+                                          : trilerp<DT, SG_LAYOUT_TILED4>(brick, F, sx, sy, sz, g[0], g[1], g[2]);
+    if (DT != SG_F32) {
+        const float s = __ldg(scales + id);
+        v.x *= s;
+        v.y *= s;
+        v.z *= s;
+    }
+    return v;
+}
+
+template <int DT>
+__device__ __forceinline__ float3 sample_time(const StreakParams &P, int layout, int stage, const int q[3],
+                                              const float g[3])
+{
+    const float3 a = sample_slot<DT>(P.F, P.slot_data[2 * stage], P.slot_scale[2 * stage], layout, q, g);
+    const float3 b = sample_slot<DT>(P.F, P.slot_data[2 * stage + 1], P.slot_scale[2 * stage + 1], layout, q, g);
+    const float al = P.alpha[stage];
+    return make_float3(lerpf(a.x, b.x, al), lerpf(a.y, b.y, al), lerpf(a.z, b.z, al));
+}
+
+__device__ __forceinline__ bool dom(const DevField &F, const int q[3], const float g[3])
+{
+    return in_axis(q[0], g[0], F.nm1[0]) && in_axis(q[1], g[1], F.nm1[1]) && in_axis(q[2], g[2], F.nm1[2]);
+}
+
+__device__ __forceinline__ float dom_out(const DevField &F, const int q[3], const float g[3])
+{
+    return fmaxf(out_axis(q[0], g[0], F.nm1[0]), fmaxf(out_axis(q[1], g[1], F.nm1[1]), out_axis(q[2], g[2], F.nm1[2])));
+}
+
+// One RK4 step of every released, live particle (stage times t, t+dt/2,
+// t+dt/2, t+dt use stage slots 0, 1, 1, 2).
+template <int DT>
+__global__ void streak_advect_kernel(const __grid_constant__ StreakParams P, int layout)
+{
+    const long long total = P.R * P.inj;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(k % P.inj);
+        if (b >= P.births || P.status[k] != SG_LINE_ACTIVE) continue;
+        Particle pr = P.state[k];
+        int c[3] = {pr.cx, pr.cy, pr.cz};
+        float f[3] = {pr.fx, pr.fy, pr.fz};
+        int q[3];
+        float g[3];
+        int st = SG_LINE_ACTIVE;
+        float margin = INFINITY;
+        float3 v = sample_time<DT>(P, layout, 0, c, f);
+        float k1[3], k2[3], k3[3], k4[3];
+        if (bad3(v)) st = SG_LINE_NANFIELD;
+        if (st == SG_LINE_ACTIVE) {
+            const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+            if (sp < P.eps) {
+                st = SG_LINE_STAGNANT;
+                margin = (P.eps - sp) / P.eps;
+            }
+        }
+        if (st == SG_LINE_ACTIVE) {
+            k1[0] = v.x * P.dtc[0]; k1[1] = v.y * P.dtc[1]; k1[2] = v.z * P.dtc[2];
+            for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k1[a], c[a], q[a], g[a]);
+            if (!dom(P.F, q, g)) { st = SG_LINE_EXIT; margin = dom_out(P.F, q, g); }
+        }
+        if (st == SG_LINE_ACTIVE) {
+            v = sample_time<DT>(P, layout, 1, q, g);
+            if (bad3(v)) st = SG_LINE_NANFIELD;
+        }
+        if (st == SG_LINE_ACTIVE) {
+            k2[0] = v.x * P.dtc[0]; k2[1] = v.y * P.dtc[1]; k2[2] = v.z * P.dtc[2];
+            for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k2[a], c[a], q[a], g[a]);
+            if (!dom(P.F, q, g)) { st = SG_LINE_EXIT; margin = dom_out(P.F, q, g); }
+        }
+        if (st == SG_LINE_ACTIVE) {
+            v = sample_time<DT>(P, layout, 1, q, g);
+            if (bad3(v)) st = SG_LINE_NANFIELD;
+        }
+        if (st == SG_LINE_ACTIVE) {
+            k3[0] = v.x * P.dtc[0]; k3[1] = v.y * P.dtc[1]; k3[2] = v.z * P.dtc[2];
+            for (int a = 0; a < 3; ++a) locate(f[a], k3[a], c[a], q[a], g[a]);
+            if (!dom(P.F, q, g)) { st = SG_LINE_EXIT; margin = dom_out(P.F, q, g); }
+        }
+        if (st == SG_LINE_ACTIVE) {
+            v = sample_time<DT>(P, layout, 2, q, g);
+            if (bad3(v)) st = SG_LINE_NANFIELD;
+        }
+        if (st == SG_LINE_ACTIVE) {
+            k4[0] = v.x * P.dtc[0]; k4[1] = v.y * P.dtc[1]; k4[2] = v.z * P.dtc[2];
+            for (int a = 0; a < 3; ++a)
+                locate(f[a], (k1[a] + k4[a] + 2.0f * (k2[a] + k3[a])) * (1.0f / 6.0f), c[a], q[a], g[a]);
+            if (!dom(P.F, q, g)) { st = SG_LINE_EXIT; margin = dom_out(P.F, q, g); }
+        }
+        if (st == SG_LINE_ACTIVE) {
+            pr.cx = q[0]; pr.cy = q[1]; pr.cz = q[2];
+            pr.fx = g[0]; pr.fy = g[1]; pr.fz = g[2];
+            pr.step += 1;
+            P.state[k] = pr;
+        } else {
+            P.status[k] = (uint8_t)st;
+            P.margin[k] = margin;
+        }
+    }
+}
+
+// Releases birth `birth` at every release point (birth 0 also resets the rest).
+__global__ void streak_release_kernel(const __grid_constant__ StreakParams P, int birth, int reset)
+{
+    const long long total = P.R * P.inj;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(k % P.inj);
+        const long long r = k / P.inj;
+        if (b != birth) {
+            if (reset) {
+                P.status[k] = 255;       // not released yet
+                P.margin[k] = INFINITY;
+            }
+            continue;
+        }
+        double p[3];
+        bool inside = true;
+        for (int a = 0; a < 3; ++a) {
+            p[a] = ((double)P.release[3 * r + a] - P.origin_d[a]) / P.spacing_d[a];
+            inside = inside && p[a] >= 0.0 && p[a] <= (double)P.F.nm1[a];
+        }
+        Particle pr;
+        int c[3] = {0, 0, 0};
+        float f[3] = {0.f, 0.f, 0.f};
+        if (inside) {
+            for (int a = 0; a < 3; ++a) {
+                const double fl = floor(p[a]);
+                c[a] = (int)fl;
+                f[a] = (float)(p[a] - fl);
+                if (f[a] >= 1.0f) { f[a] = 0.0f; c[a] += 1; }
+            }
+        }
+        pr.cx = c[0]; pr.cy = c[1]; pr.cz = c[2];
+        pr.fx = f[0]; pr.fy = f[1]; pr.fz = f[2];
+        pr.line = (uint32_t)r;
+        pr.step = 0;
+        P.state[k] = pr;
+        P.status[k] = inside ? SG_LINE_ACTIVE : SG_LINE_OUT;
+        P.margin[k] = INFINITY;
+    }
+}
+
+// Per release point: live particles (low 40 bits) and runs of consecutive live
+// particles (high 24 bits), packed for one scan.
+__global__ void streak_count_kernel(const uint8_t *status, long long R, int inj, int births,
+                                    unsigned long long *packed)
+{
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (long long)gridDim.x * blockDim.x) {
+        unsigned long long live = 0, runs = 0;
+        bool prev = false;
+        for (int b = 0; b < births; ++b) {
+            const bool l = status[r * inj + b] == SG_LINE_ACTIVE;
+            live += l;
+            runs += (l && !prev);
+            prev = l;
+        }
+        packed[r] = live + (runs << 40);
+    }
+}
+
+// Exclusive scan of packed[0..n) into excl (n+1 entries); single pass per
+// 1024-entry chunk with a carried prefix (n is the number of release points).
+__global__ void scan_u64_kernel(const unsigned long long *in, long long n, unsigned long long *excl, int64_t *totals)
+{
+    __shared__ unsigned long long ws[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long base = 0; base < n; base += blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const unsigned long long v = i < n ? in[i] : 0ull;
+        unsigned long long x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(SG_FULL_MASK, x, o);
+            if ((int)lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = lane < (blockDim.x >> 5) ? ws[lane] : 0ull;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(SG_FULL_MASK, w, o);
+                if ((int)lane >= o) w += y;
+            }
+            ws[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long before = carry + (warp ? ws[warp - 1] : 0ull) + x - v;
+        if (i < n) excl[i] = before;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        excl[n] = carry;
+        totals[0] = (int64_t)(carry & ((1ull << 40) - 1));   // vertices
+        totals[1] = (int64_t)(carry >> 40);                  // lines
+        totals[2] = 0;
+    }
+}
+
+// One thread per release point: its runs become lines.
+__global__ void streak_gather_kernel(const Particle *state, const uint8_t *status, long long R, int inj, int births,
+                                     const unsigned long long *excl, DevField F, int64_t *offsets, float *vertices,
+                                     uint8_t *st_out, float *mg_out, int32_t *source)
+{
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (long long)gridDim.x * blockDim.x) {
+        long long v = (long long)(excl[r] & ((1ull << 40) - 1));
+        long long line = (long long)(excl[r] >> 40);
+        bool prev = false;
+        for (int b = 0; b < births; ++b) {
+            const long long k = r * inj + b;
+            const bool l = status[k] == SG_LINE_ACTIVE;
+            if (l && !prev) {
+                if (offsets) offsets[line] = v;
+                if (st_out) st_out[line] = SG_LINE_ACTIVE;
+                if (mg_out) mg_out[line] = INFINITY;
+                if (source) source[line] = (int32_t)r;
+                ++line;
+            }
+            if (l) {
+                if (vertices) {
+                    const Particle p = state[k];
+                    vertices[3 * v] = fmaf(F.spacing[0], (float)p.cx + p.fx, F.origin[0]);
+                    vertices[3 * v + 1] = fmaf(F.spacing[1], (float)p.cy + p.fy, F.origin[1]);
+                    vertices[3 * v + 2] = fmaf(F.spacing[2], (float)p.cz + p.fz, F.origin[2]);
+                }
+                ++v;
+            }
+            prev = l;
+        }
+    }
+    if (offsets && blockIdx.x == 0 && threadIdx.x == 0) offsets[excl[R] >> 40] = (int64_t)(excl[R] & ((1ull << 40) - 1));
+}
+
+static StreakParams streak_params(const sg_tracer *t)
+{
+    StreakParams P;
+    memset(&P, 0, sizeof P);
+    const sg_field *f = t->field;
+    P.F = field_view(f, 0);
+    for (int i = 0; i < 6; ++i) {
+        P.slot_data[i] = f->slot_data[0];
+        P.slot_scale[i] = f->slot_scales[0];
+    }
+    P.state = t->sk_state;
+    P.status = t->sk_status;
+    P.margin = t->sk_margin;
+    P.release = t->seeds;
+    P.R = t->n_seeds;
+    P.inj = t->p.inject_steps;
+    P.births = t->births;
+    for (int a = 0; a < 3; ++a) {
+        P.dtc[a] = (float)(t->p.dt / f->desc.spacing[a]);
+        P.origin_d[a] = f->desc.origin[a];
+        P.spacing_d[a] = f->desc.spacing[a];
+    }
+    P.eps = t->p.eps;
+    return P;
+}
+
+static int grid_for(const sg_tracer *t, long long n)
+{
+    long long g = (n + 255) / 256;
+    const long long cap = (long long)t->ctx->sm_count * 16;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+sg_status streak_upload(sg_tracer *t, cudaStream_t s)
+{
+    t->births = 1;
+    t->steps_done = 0;
+    StreakParams P = streak_params(t);
+    const long long total = t->n_seeds * (long long)t->p.inject_steps;
+    if (total == 0) return SG_OK;
+    streak_release_kernel<<<grid_for(t, total), 256, 0, s>>>(P, 0, 1);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+// Slice pair of time t: s = ceil(t/slice_dt) - 1 (>= 0), alpha = t/slice_dt - s.
+static void slice_pair(double t, double sdt, int *s_out, double *alpha_out)
+{
+    const double u = t / sdt;
+    long long s = (long long)ceil(u) - 1;
+    if (s < 0) s = 0;
+    *s_out = (int)s;
+    *alpha_out = u - (double)s;
+}
+
+sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s)
+{
+    sg_field *f = t->field;
+    const double dt = t->p.dt, sdt = f->desc.slice_dt;
+    for (int i = 0; i < n_steps; ++i) {
+        const int j = t->steps_done + 1;
+        const double t0 = (double)(j - 1) * dt;
+        const double times[3] = {t0, t0 + 0.5 * dt, t0 + dt};
+        StreakParams P = streak_params(t);
+        for (int st = 0; st < 3; ++st) {
+            int sl;
+            double al;
+            slice_pair(times[st], sdt, &sl, &al);
+            for (int h = 0; h < 2; ++h) {
+                const int slice = sl + h;
+                const int slot = slice % f->desc.n_slots;
+                SG_CHECK(f->slot_slice[slot] == slice, SG_ERR_STATE,
+                         "step %d needs time slice %d, which is not resident (slot %d holds %d)", j, slice, slot,
+                         f->slot_slice[slot]);
+                SG_CUDA(cudaStreamWaitEvent(s, f->slot_ready[slot], 0));
+                P.slot_data[2 * st + h] = f->slot_data[slot];
+                P.slot_scale[2 * st + h] = f->slot_scales[slot];
+            }
+            P.alpha[st] = (float)al;
+        }
+        const long long total = t->n_seeds * (long long)t->p.inject_steps;
+        if (total > 0) {
+            if (f->desc.dtype == SG_F32) streak_advect_kernel<SG_F32><<<grid_for(t, total), 256, 0, s>>>(P, f->desc.layout);
+            else if (f->desc.dtype == SG_BF16)
+                streak_advect_kernel<SG_BF16><<<grid_for(t, total), 256, 0, s>>>(P, f->desc.layout);
+            else streak_advect_kernel<SG_F16><<<grid_for(t, total), 256, 0, s>>>(P, f->desc.layout);
+            SG_CUDA(cudaGetLastError());
+            if (j < t->p.inject_steps) {
+                streak_release_kernel<<<grid_for(t, total), 256, 0, s>>>(P, j, 0);
+                SG_CUDA(cudaGetLastError());
+            }
+        }
+        // later streams into these slots wait for this step
+        for (int st = 0; st < 3; ++st)
+            for (int h = 0; h < 2; ++h) {
+                int sl;
+                double al;
+                slice_pair(times[st], sdt, &sl, &al);
+                SG_CUDA(cudaEventRecord(f->slot_used[(sl + h) % f->desc.n_slots], s));
+            }
+        if (j < t->p.inject_steps) t->births = j + 1;
+        t->steps_done = j;
+    }
+    t->scanned = false;
+    if (any_active) {
+        SG_CUDA(cudaStreamSynchronize(s));
+        *any_active = t->n_seeds > 0 ? 1 : 0;
+    }
+    return SG_OK;
+}
+
+sg_status launch_streak_scan(sg_tracer *t, cudaStream_t s)
+{
+    const long long R = t->n_seeds;
+    unsigned long long *packed = t->block_sums;      // R + 2 entries are carved for this
+    unsigned long long *excl = reinterpret_cast<unsigned long long *>(t->offsets);
+    if (R > 0) {
+        streak_count_kernel<<<grid_for(t, R), 256, 0, s>>>(t->sk_status, R, t->p.inject_steps, t->births, packed);
+        SG_CUDA(cudaGetLastError());
+    }
+    scan_u64_kernel<<<1, 1024, 0, s>>>(packed, R, excl, t->totals);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+sg_status launch_streak_gather(sg_tracer *t, int64_t *offsets, float *vertices, uint8_t *status, float *margin,
+                               int32_t *source, cudaStream_t s)
+{
+    const long long R = t->n_seeds;
+    const unsigned long long *excl = reinterpret_cast<const unsigned long long *>(t->offsets);
+    streak_gather_kernel<<<grid_for(t, R > 0 ? R : 1), 256, 0, s>>>(t->sk_state, t->sk_status, R, t->p.inject_steps,
+                                                                     t->births, excl, field_view(t->field, 0), offsets,
+                                                                     vertices, status, margin, source);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+sg_status launch_streak_release(sg_tracer *t, int birth, cudaStream_t s)
+{
+    StreakParams P = streak_params(t);
+    const long long total = t->n_seeds * (long long)t->p.inject_steps;
+    if (total == 0) return SG_OK;
+    streak_release_kernel<<<grid_for(t, total), 256, 0, s>>>(P, birth, 0);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+}  // namespace sg

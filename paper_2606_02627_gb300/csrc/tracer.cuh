@@ -1,0 +1,102 @@
+// Internal state of a tracer and the launchers shared by its translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace sg {
+
+// Everything a streamline kernel needs, passed by value (__grid_constant__).
+struct LineParams {
+    DevField F;                  // field slot
+    const float *seeds;          // n x 3 world (per-seed kernel)
+    Particle *q;                 // brick-sorted queue of the round
+    Particle *o;                 // outgoing records (hand-offs, re-queues)
+    Particle *park;              // records that reached the step horizon
+    Ctrl *ctrl;
+    float *slab;                 // [line][W][3] world vertices
+    uint32_t *line_len;          // vertices per line
+    uint8_t *line_status;
+    float *line_margin;
+    long long W;                 // max_steps + 1
+    long long n_lines;
+    float dtc[3];                // dt / spacing: cells per unit velocity
+    float eps;
+    float tie_cells;
+    float tie_eps_rel;
+    uint32_t max_steps;
+    uint32_t steps_per_round;
+    double origin_d[3];
+    double spacing_d[3];
+};
+
+enum { EV_NONE = 0, EV_STOP = 1, EV_APPEND = 2, EV_PARK = 3 };
+
+}  // namespace sg
+
+struct sg_tracer {
+    sg_context *ctx;
+    sg_field *field;
+    sg_tracer_params p;
+    int64_t capacity;
+    int64_t n_seeds;
+    char *ws;
+    size_t ws_bytes;
+    int nb;
+    // streamline state
+    float *seeds;
+    float *slab;
+    uint32_t *line_len;
+    uint8_t *line_status;
+    float *line_margin;
+    sg::Particle *q;
+    sg::Particle *o;
+    sg::Particle *park;
+    sg::Ctrl *ctrl;
+    uint32_t *brick_count;
+    uint32_t *brick_cursor;
+    // compaction
+    int64_t *offsets;            // capacity + 1
+    unsigned long long *block_sums;
+    int64_t *totals;             // [0] vertices, [1] lines, [2] steps
+    int64_t *host_totals;        // page-locked copy of totals
+    bool scanned;
+    // streaklines
+    int64_t n_release;
+    int32_t births;              // births released so far
+    int32_t steps_done;          // advection steps done
+    sg::Particle *sk_state;      // [release][inject] particle state (cell, frac, steps in .step)
+    uint8_t *sk_status;          // [release][inject]
+    float *sk_margin;            // [release][inject]
+    uint32_t *sk_seglen;         // [release][inject]: run length at each run start, else 0
+    // schedule
+    int block;
+    int grid;
+    uint32_t horizon;            // step horizon of the next call
+    bool traced;
+    // CUDA graph of the round loop
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    bool graph_ready;
+};
+
+namespace sg {
+
+sg_status launch_upload(sg_tracer *t, cudaStream_t s);
+sg_status launch_per_seed(sg_tracer *t, cudaStream_t s);
+sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStream_t s, bool in_graph,
+                     unsigned long long cond_handle, int mode);
+sg_status launch_round(sg_tracer *t, cudaStream_t s);
+sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s);
+sg_status launch_iota(int32_t *dst, int64_t n, cudaStream_t s);
+sg_status streak_upload(sg_tracer *t, cudaStream_t s);
+sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s);
+sg_status launch_scan_lengths(sg_tracer *t, cudaStream_t s);
+sg_status launch_gather_lines(sg_tracer *t, int64_t *offsets, float *vertices, uint8_t *status, float *margin,
+                              cudaStream_t s);
+sg_status launch_streak_release(sg_tracer *t, int birth, cudaStream_t s);
+sg_status launch_streak_scan(sg_tracer *t, cudaStream_t s);
+sg_status launch_streak_gather(sg_tracer *t, int64_t *offsets, float *vertices, uint8_t *status, float *margin,
+                               int32_t *source, cudaStream_t s);
+LineParams line_params(const sg_tracer *t);
+
+}  // namespace sg
