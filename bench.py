@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark: RK4 particle-steps/s of brick-decomposed steady streamlines.
+
+Workload (one step = the whole hot path on one batch): a 512^3 FP32 vec3
+synthetic-turbulence field (256 divergence-free Fourier modes, |k|^-5/3
+amplitudes, SplitMix64 seed 1) resident in HBM is cut into 4x4x4 bricks with a
+one-cell ghost shell and encoded to the benchmarked storage type; 1M seeds
+(uniform over the grid) are uploaded and binned into per-brick queues; RK4
+with h = 0.5 cell runs to max 2000 steps (exit / |v| < 1e-6 / cap) with
+cross-brick hand-off queues; the lines are compacted to CSR.
+
+`value` is the BF16-field persistent form (the precision form); the FP32
+persistent form, the plain FP32 per-seed kernel and (optionally) the
+one-launch-per-step kernel of Listing 1 are timed in the same run under
+`variants`.  `e2e` repeats the headline through the C ABI with the seeds
+copied from page-locked host memory and the CSR lines written to page-locked
+host memory inside the timed region.
+
+Multi-GPU (torchrun): every rank traces its own 1M seeds on its own copy of the
+field (independent work, weak scaling); only the timing barrier and the
+max-over-ranks reduction cross ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GATHER_BYTES = {"f32": 4 * 8 * 3 * 4 + 12, "bf16": 4 * 8 * 3 * 2 + 12, "f16": 4 * 8 * 3 * 2 + 12}
+METRIC = "RK4 particle-steps/s"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="samples per axis")
+    ap.add_argument("--seeds", type=int, default=1 << 20)
+    ap.add_argument("--max-steps", type=int, default=2000)
+    ap.add_argument("--h", type=float, default=0.5)
+    ap.add_argument("--dtype", default="bf16", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--layout", default="linear")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--per-step", action="store_true", help="also time the one-launch-per-step kernel")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
+    ap.add_argument("--schedule", default="", help="block,blocks_per_sm,steps_per_round")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("advect.cu", "common.cuh", "tracer.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2606_02627_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_step(dtype):
+    """DRAM bytes per particle-step of the round kernel from the committed ncu
+    summary, or None if it is missing or the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", f"round_kernel_{dtype}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_hash") != kernel_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_particle_step"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.f:
+            return None
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid:
+                continue
+            rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(F_host, grid, seeds, dt, max_steps, seconds):
+    """Oracle particle-steps/s on the host cores over a bounded prefix of the seeds."""
+    import oracle
+    nthreads = oracle.default_threads()
+    n0 = min(len(seeds), max(nthreads * 8, 64))
+    t = time.perf_counter()
+    L = oracle.trace_streamlines(F_host, grid.origin, grid.spacing, seeds[:n0], dt, max_steps, eps=1e-6,
+                                 nthreads=nthreads)
+    t0 = time.perf_counter() - t
+    n = int(min(len(seeds), max(n0, n0 * seconds / max(t0, 1e-3))))
+    if n > n0:
+        t = time.perf_counter()
+        L = oracle.trace_streamlines(F_host, grid.origin, grid.spacing, seeds[:n], dt, max_steps, eps=1e-6,
+                                     nthreads=nthreads)
+        t0 = time.perf_counter() - t
+    steps = int(L.steps().sum())
+    return steps / t0, nthreads, n, steps, t0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    from paper_2606_02627_gb300 import inputs
+
+    n = args.n
+    grid = inputs.cube_grid(n)
+    config = {"workload": f"steady streamlines, {n}^3 FP32 vec3 synthetic turbulence (256 modes, seed 1), "
+                          f"4x4x4 bricks + 1-cell ghost, {args.seeds} seeds, RK4 h={args.h} cell, "
+                          f"max {args.max_steps} steps",
+              "field": f"{n}^3", "bricks": "4x4x4", "seeds_per_gpu": args.seeds, "max_steps": args.max_steps,
+              "h_cells": args.h, "field_storage": args.dtype, "layout": args.layout,
+              "l2": "inputs larger than L2 (field 1.6 GB, bricks 0.9-1.8 GB, slabs 24 GB)",
+              "parallelism": f"replicas x{world} (seeds per rank, field replicated)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the reference arm is the FP64 oracle on the host cores, on a bounded prefix of the seeds
+        import oracle
+        modes = inputs.turbulence_modes(1)
+        F = inputs.turbulence_field(grid, modes, device="cuda" if torch.cuda.is_available() else None)
+        F_host = F.cpu().numpy()
+        del F
+        dt = args.h / oracle.max_speed(F_host, grid.spacing)
+        seeds = inputs.uniform_seeds(grid, args.seeds, 1)
+        rates = []
+        info = None
+        for it in range(args.warmup + args.steps):
+            rate, cores, ns, steps, secs = cpu_oracle_rate(F_host, grid, seeds, dt, args.max_steps,
+                                                           args.cpu_seconds / 2)
+            if it >= args.warmup:
+                rates.append(rate)
+            info = (cores, ns, steps, secs)
+        v = statistics.median(rates)
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+               "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64", "data": "synthetic", "config": config,
+               "cpu_baseline": {"value": v, "unit": UNIT, "cores": info[0], "kind": "oracle",
+                                "sample": f"first {info[1]} of {args.seeds} seeds per step ({info[2]} particle-steps, "
+                                          f"{info[3]:.1f} s)"},
+               "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    from paper_2606_02627_gb300 import api
+    from paper_2606_02627_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    stream = torch.cuda.Stream(device=dev)
+    ctx = api.Context(local)
+
+    modes = inputs.turbulence_modes(1)
+    with torch.cuda.stream(stream):
+        F = inputs.turbulence_field(grid, modes, device=dev)
+    stream.synchronize()
+    sched = {}
+    if args.schedule:
+        b, bps, spr = (int(x) for x in args.schedule.split(","))
+        sched = dict(block_size=b, blocks_per_sm=bps, steps_per_round=spr)
+
+    seeds_np = inputs.uniform_seeds(grid, args.seeds, 1 + 1000 * rank)
+    seeds_dev = torch.from_numpy(seeds_np).to(dev)
+    seeds_pin = torch.from_numpy(seeds_np).pin_memory()
+
+    def make(dtype, layout, kernel):
+        fld = api.Field(ctx, grid.dims, grid.origin, grid.spacing,
+                        bricks=(1, 1, 1) if layout == "global" else (4, 4, 4), dtype=dtype, layout=layout)
+        fld.set_global(F, stream=stream)
+        tr = api.Tracer(ctx, fld, capacity=args.seeds, dt=dt, max_steps=args.max_steps, kernel=kernel,
+                        **(sched if kernel == "persistent" else {}))
+        return fld, tr
+
+    # dt from the FP32 field's largest speed: every step is at most h cells
+    probe = api.Field(ctx, grid.dims, grid.origin, grid.spacing, bricks=(4, 4, 4), dtype="f32")
+    probe.set_global(F, stream=stream)
+    vref = probe.max_speed(stream=stream)
+    dt = args.h / vref
+    del probe
+
+    def one_step(fld, tr, out_off, out_vert, out_st, seeds):
+        fld.set_global(F, stream=stream)                     # a1: bricks, ghosts, encode
+        tr.upload_seeds(seeds, stream=stream)               # a2: seeds -> per-brick queues
+        tr.trace(stream=stream)                             # a3-a7: rounds of the persistent kernel
+        L = api.L
+        api.call("sg_tracer_get_lines", tr.h, None, None, api._ptr(out_off), api._ptr(out_vert),
+                 api._ptr(out_st), None, None, api._stream(stream))    # a8: CSR
+
+    def timed(fld, tr, warmup, steps, seeds, host_out=False):
+        nl, nv = None, None
+        # size the outputs from one untimed run
+        one_step(fld, tr, None, None, None, seeds_dev)
+        nl, nv = tr.sizes(stream=stream)
+        tot = tr.total_steps(stream=stream)
+        kw = dict(pin_memory=True) if host_out else dict(device=dev)
+        off = torch.empty(nl + 1, dtype=torch.int64, **kw)
+        vert = torch.empty((max(nv, 1), 3), dtype=torch.float32, **kw)
+        st = torch.empty(max(nl, 1), dtype=torch.uint8, **kw)
+        for _ in range(warmup):
+            one_step(fld, tr, off, vert, st, seeds)
+        stream.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            one_step(fld, tr, off, vert, st, seeds)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            s = torch.tensor([float(tot)], device=dev)
+            dist.all_reduce(s)
+            tot_all = int(s.item())
+        else:
+            tot_all = tot
+        ok = tr.check(stream=stream)
+        bytes_out = off.numel() * 8 + nv * 12 + nl
+        return ms, tot, tot_all, bytes_out
+
+    results = {}
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+
+    # headline: BF16 (or the chosen storage) persistent form
+    fld, tr = make(args.dtype, args.layout, "persistent")
+    with Clocks(uuid) as clk:
+        ms, tot, tot_all, _ = timed(fld, tr, args.warmup, args.steps, seeds_dev)
+    clocks = clk.summary()
+    value = tot_all / (ms / 1e3)
+    results["headline"] = (ms, tot)
+
+    # roofline of the dominant kernel: round kernel time by CUDA events (host-driven rounds)
+    tr.upload_seeds(seeds_dev, stream=stream)
+    fld.set_global(F, stream=stream)
+    kms, launches = tr.trace_timed(stream=stream)
+    ksteps = tr.total_steps(stream=stream)
+    hbm, peak_kind = peaks()
+    bps = GATHER_BYTES[args.dtype]
+    achieved = ksteps * bps / (kms / 1e3) / 1e9
+    tps = traffic_per_step(args.dtype)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": (tps * ksteps / launches) if tps else None,
+                "kernel": "round_kernel (persistent advection)", "peak_source": f"{peak_kind} hbm_gbs",
+                "model": f"gather bytes: 4 samples x 8 corners x 3 comps x elem + 12 B vertex = {bps} B "
+                         f"per particle-step (L1/L2 hits counted at HBM price)",
+                "kernel_ms_per_launch": kms / launches, "launches": launches,
+                "particle_steps_per_launch": ksteps / launches}
+
+    # e2e through the C ABI: seeds from pinned host, CSR lines to pinned host, inside the timed region
+    ems, _, etot_all, d2h = timed(fld, tr, 1, max(1, min(args.steps, 3)), seeds_pin, host_out=True)
+    e2e = {"value": etot_all / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(seeds_pin.numel() * 4),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": ems}
+    del tr, fld
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if not args.no_variants:
+        runs = [("f32_persistent", "f32", args.layout, "persistent"), ("f32_per_seed", "f32", "global", "per_seed")]
+        if args.dtype != "bf16":
+            runs.insert(0, ("bf16_persistent", "bf16", args.layout, "persistent"))
+        if args.per_step:
+            runs.append(("f32_per_step", "f32", args.layout, "per_step"))
+        for name, dtp, lay, ker in runs:
+            f2, t2 = make(dtp, lay, ker)
+            vms, vtot, vtot_all, _ = timed(f2, t2, 1, 2, seeds_dev)
+            variants[name] = {"value": vtot_all / (vms / 1e3), "ms_per_step": vms, "particle_steps": vtot,
+                              "field_storage": dtp, "kernel": ker}
+            del t2, f2
+            torch.cuda.empty_cache()
+        variants[f"{args.dtype}_persistent"] = {"value": value, "ms_per_step": ms, "particle_steps": tot,
+                                                "field_storage": args.dtype, "kernel": "persistent"}
+
+    cpu = None
+    if rank == 0:
+        F_host = F.cpu().numpy()
+        rate, cores, ns, steps, secs = cpu_oracle_rate(F_host, grid, seeds_np, dt, args.max_steps, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {ns} of {args.seeds} seeds of the same workload on the FP32 field "
+                         f"({steps} particle-steps in {secs:.1f} s)"}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+               "particle_steps_per_step": tot_all, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": None, "clocks": clocks, "variants": variants}
+        # kernels of ours per timed step: set_global (2-3), upload (1), prepare (1), bin (4) + rounds x (1 + 4),
+        # scan (3), gather (1)
+        out["gpu_launches"] = int(args.steps * (3 + 1 + 1 + 4 + launches * 5 + 3 + 1))
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

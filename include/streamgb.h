@@ -60,10 +60,14 @@ enum {
  * Interpolation and integration are FP32 in every case. */
 enum { SG_F32 = 0, SG_BF16 = 1, SG_F16 = 2 };
 
-/* Sample layout inside a brick (both: 16 B per FP32 sample, 8 B per BF16/FP16
- * sample, components x, y, z and one pad).  LINEAR is x-fastest; TILED4 groups
- * 4x4x4 samples contiguously (tile-major, x-fastest inside a tile). */
-enum { SG_LAYOUT_LINEAR = 0, SG_LAYOUT_TILED4 = 1 };
+/* Sample layout inside a brick.  A sample is x, y, z and one pad: 16 B in
+ * FP32, 8 B in BF16/FP16.  LINEAR is x-fastest; TILED4 groups 4x4x4 samples
+ * contiguously (tile-major, x-fastest inside a tile).  CELL8 stores, for every
+ * cell of the brick (ghost cells included, (n+2)^3 of them), the eight corner
+ * samples of that cell contiguously (x fastest, then y, then z): 8x the
+ * samples, so that one interpolation reads one 64 B (BF16/FP16) or 128 B
+ * (FP32) record instead of eight scattered samples. */
+enum { SG_LAYOUT_LINEAR = 0, SG_LAYOUT_TILED4 = 1, SG_LAYOUT_CELL8 = 2 };
 
 /* Line status (uint8 per line).  Bit 7 (SG_LINE_TIE) marks a boundary tie: a
  * line that stopped by EXIT with its offending point less than tie_cells
@@ -142,7 +146,7 @@ typedef struct {
     int32_t bricks[3];    /* bricks per axis, >= 1; the last brick must own a cell */
     int32_t ghost;        /* ghost layers; must be 1                            */
     int32_t dtype;        /* SG_F32, SG_BF16, SG_F16                            */
-    int32_t layout;       /* SG_LAYOUT_LINEAR, SG_LAYOUT_TILED4, SG_FIELD_GLOBAL */
+    int32_t layout;       /* SG_LAYOUT_LINEAR / _TILED4 / _CELL8, SG_FIELD_GLOBAL */
     int32_t n_slots;      /* resident slices, >= 1                              */
     double slice_dt;      /* time between slices (unsteady fields), > 0         */
 } sg_field_desc;
@@ -252,6 +256,14 @@ sg_status sg_tracer_trace(sg_tracer *t, void *stream);
  * asynchronous trace stopped at its round cap, else SG_OK.  rounds (nullable)
  * receives the number of rounds of the last trace. */
 sg_status sg_tracer_check(sg_tracer *t, int32_t *rounds, void *stream);
+
+/* Measurement form of sg_tracer_trace: the same kernels on the same data, but
+ * the rounds are driven from the host with a CUDA event pair around every
+ * advection-kernel launch, so that the kernel's own time can be read (event
+ * record nodes cannot sit inside the graph's while-node).  Synchronous.
+ * kernel_ms receives the summed advection-kernel time, launches the number of
+ * advection-kernel launches (both nullable). */
+sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int32_t *launches, void *stream);
 
 /* Line readback (getLines of Fig. 4), compacted to CSR: line i's vertices
  * are vertices[offsets[i] .. offsets[i+1]) (world xyz float32).  For

@@ -26,7 +26,7 @@ ERR_NAMES = {0: "SG_OK", -1: "SG_ERR_INVALID_ARG", -2: "SG_ERR_OOM", -3: "SG_ERR
              -4: "SG_ERR_ROUND_LIMIT", -5: "SG_ERR_TIMEOUT", -6: "SG_ERR_STATE", -7: "SG_ERR_UNSUPPORTED"}
 
 SG_F32, SG_BF16, SG_F16 = 0, 1, 2
-SG_LAYOUT_LINEAR, SG_LAYOUT_TILED4, SG_FIELD_GLOBAL = 0, 1, 16
+SG_LAYOUT_LINEAR, SG_LAYOUT_TILED4, SG_LAYOUT_CELL8, SG_FIELD_GLOBAL = 0, 1, 2, 16
 SG_STREAMLINE, SG_STREAKLINE = 0, 1
 SG_KERNEL_PERSISTENT, SG_KERNEL_PER_SEED, SG_KERNEL_PER_STEP = 0, 1, 2
 SG_LINE_ACTIVE, SG_LINE_MAXSTEPS, SG_LINE_EXIT, SG_LINE_STAGNANT = 0, 1, 2, 3
@@ -83,6 +83,7 @@ SIGNATURES = {
     "sg_tracer_step": ([P, i32, ctypes.POINTER(i32), P], i32),
     "sg_tracer_trace": ([P, P], i32),
     "sg_tracer_check": ([P, ctypes.POINTER(i32), P], i32),
+    "sg_tracer_trace_timed": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), P], i32),
     "sg_tracer_get_lines": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P, P, P], i32),
     "sg_tracer_total_steps": ([P, ctypes.POINTER(i64), P], i32),
 }

@@ -15,7 +15,8 @@ from . import _lib as L
 from ._lib import call
 
 DTYPES = {"f32": L.SG_F32, "bf16": L.SG_BF16, "f16": L.SG_F16}
-LAYOUTS = {"linear": L.SG_LAYOUT_LINEAR, "tiled4": L.SG_LAYOUT_TILED4, "global": L.SG_FIELD_GLOBAL}
+LAYOUTS = {"linear": L.SG_LAYOUT_LINEAR, "tiled4": L.SG_LAYOUT_TILED4, "cell8": L.SG_LAYOUT_CELL8,
+           "global": L.SG_FIELD_GLOBAL}
 KERNELS = {"persistent": L.SG_KERNEL_PERSISTENT, "per_seed": L.SG_KERNEL_PER_SEED, "per_step": L.SG_KERNEL_PER_STEP}
 STATUS_NAMES = {0: "ACTIVE", 1: "MAXSTEPS", 2: "EXIT", 3: "STAGNANT", 4: "NANFIELD", 5: "OUT", 6: "HALO"}
 
@@ -202,6 +203,14 @@ class Tracer:
 
     def trace(self, stream=None):
         call("sg_tracer_trace", self.h, _stream(stream))
+
+    def trace_timed(self, stream=None):
+        """Host-driven rounds with CUDA events around each advection kernel:
+        returns (summed kernel ms, launches)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int32()
+        call("sg_tracer_trace_timed", self.h, ctypes.byref(ms), ctypes.byref(n), _stream(stream))
+        return ms.value, n.value
 
     def check(self, stream=None) -> int:
         r = ctypes.c_int32()

@@ -530,7 +530,11 @@ sg_status launch_round(sg_tracer *t, cudaStream_t s)
     LineParams P = line_params(t);
     const int dt = t->field->desc.dtype, lay = t->field->desc.layout;
     const int k = t->p.kernel;
-    if (lay == SG_LAYOUT_LINEAR) {
+    if (lay == SG_LAYOUT_CELL8) {
+        if (dt == SG_F32) launch_round_t<SG_F32, SG_LAYOUT_CELL8>(P, t->grid, t->block, k, s);
+        else if (dt == SG_BF16) launch_round_t<SG_BF16, SG_LAYOUT_CELL8>(P, t->grid, t->block, k, s);
+        else launch_round_t<SG_F16, SG_LAYOUT_CELL8>(P, t->grid, t->block, k, s);
+    } else if (lay == SG_LAYOUT_LINEAR) {
         if (dt == SG_F32) launch_round_t<SG_F32, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);
         else if (dt == SG_BF16) launch_round_t<SG_BF16, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);
         else launch_round_t<SG_F16, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);

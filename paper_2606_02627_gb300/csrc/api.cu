@@ -415,6 +415,78 @@ extern "C" sg_status sg_tracer_trace(sg_tracer *t, void *stream)
     return run_call(t, target, n, s);
 }
 
+extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int32_t *launches, void *stream)
+{
+    SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
+    SG_CHECK(t->p.mode == SG_STREAMLINE, SG_ERR_STATE, "trace() is for streamlines");
+    SG_CUDA(cudaSetDevice(t->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    SG_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_error(ce, "cudaEventCreate");
+    }
+    double total = 0.0;
+    int32_t n_launch = 0;
+    sg_status st = SG_OK;
+    if (t->n_seeds > 0 && t->p.kernel == SG_KERNEL_PER_SEED) {
+        if (t->traced) {
+            set_error("the per-seed kernel traces once per upload");
+            st = SG_ERR_STATE;
+        }
+        if (st == SG_OK && (ce = cudaEventRecord(e0, s)) != cudaSuccess) st = cuda_error(ce, "cudaEventRecord");
+        if (st == SG_OK) st = launch_per_seed(t, s);
+        if (st == SG_OK && (ce = cudaEventRecord(e1, s)) != cudaSuccess) st = cuda_error(ce, "cudaEventRecord");
+        if (st == SG_OK && (ce = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_error(ce, "cudaEventSynchronize");
+        float ms = 0.f;
+        if (st == SG_OK && (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) st = cuda_error(ce, "elapsed");
+        total = ms;
+        n_launch = 1;
+        t->traced = true;
+        t->scanned = false;
+    } else if (t->n_seeds > 0) {
+        const uint32_t target = (uint32_t)t->p.max_steps;
+        const uint32_t n = target > t->horizon ? target - t->horizon : 0;
+        t->horizon = target;
+        uint64_t cap = (uint64_t)n + 2;
+        if (t->p.max_rounds > 0 && (uint64_t)t->p.max_rounds < cap) cap = (uint64_t)t->p.max_rounds;
+        st = launch_prepare_call(t, target, (uint32_t)cap, s);
+        if (st == SG_OK) st = launch_bin(t, t->park, &t->ctrl->p_count, s, false, 0ull, 0);
+        Ctrl c;
+        while (st == SG_OK) {
+            if ((ce = cudaMemcpyAsync(&c, t->ctrl, sizeof c, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+                (ce = cudaStreamSynchronize(s)) != cudaSuccess) {
+                st = cuda_error(ce, "ctrl readback");
+                break;
+            }
+            if (c.q_count == 0 || c.round >= c.max_rounds) break;
+            if ((ce = cudaEventRecord(e0, s)) != cudaSuccess) { st = cuda_error(ce, "cudaEventRecord"); break; }
+            st = launch_round(t, s);
+            if (st) break;
+            if ((ce = cudaEventRecord(e1, s)) != cudaSuccess) { st = cuda_error(ce, "cudaEventRecord"); break; }
+            st = launch_bin(t, t->o, &t->ctrl->o_count, s, false, 0ull, 1);
+            if (st) break;
+            if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_error(ce, "cudaEventSynchronize"); break; }
+            float ms = 0.f;
+            if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) { st = cuda_error(ce, "elapsed"); break; }
+            total += ms;
+            ++n_launch;
+        }
+        t->scanned = false;
+        if (st == SG_OK && c.q_count > 0) {
+            set_error("the round cap stopped the trace with particles left");
+            st = SG_ERR_ROUND_LIMIT;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (kernel_ms) *kernel_ms = total;
+    if (launches) *launches = n_launch;
+    return st;
+}
+
 extern "C" sg_status sg_tracer_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, void *stream)
 {
     SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");

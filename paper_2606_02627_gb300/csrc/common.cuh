@@ -68,6 +68,7 @@ struct DevField {
     int B[3];                // bricks per axis
     int S[3];                // stored samples per brick per axis (n + 3)
     int T[3];                // tiles of 4 per axis (tiled layout)
+    int C[3];                // cells per brick per axis (cell-record layout: n + 2)
     long long brick_elems;   // samples per brick (with tile padding)
     long long brick_stride;  // samples from one brick's start to the next
     float origin[3];
@@ -193,32 +194,20 @@ struct Offsets {
 inline __host__ __device__ long long storage_index(int layout, int x, int y, int z, const DevField &F)
 {
     if (layout == SG_LAYOUT_LINEAR) return ((long long)z * F.S[1] + y) * F.S[0] + x;
+    if (layout == SG_LAYOUT_CELL8) {
+        // the copy of sample (x,y,z) held by the cell whose lower corner it is
+        // (the last cell for the upper layer)
+        const int cx = x < F.C[0] ? x : F.C[0] - 1, cy = y < F.C[1] ? y : F.C[1] - 1, cz = z < F.C[2] ? z : F.C[2] - 1;
+        const int corner = (x - cx) | ((y - cy) << 1) | ((z - cz) << 2);
+        return (((long long)cz * F.C[1] + cy) * F.C[0] + cx) * 8 + corner;
+    }
     return (((long long)(z >> 2) * F.T[1] + (y >> 2)) * F.T[0] + (x >> 2)) * 64 + ((z & 3) * 4 + (y & 3)) * 4 + (x & 3);
 }
 
-// Trilinear interpolation inside one brick: (sx, sy, sz) is the storage index
-// of the lower corner, (fx, fy, fz) the fractions.  Returns the undecoded-scale
-// value (multiply by the brick scale for world units).
-template <int DT, int LAYOUT>
-__device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict__ brick, const DevField &F,
-                                          int sx, int sy, int sz, float fx, float fy, float fz)
+__device__ __forceinline__ float3 lerp8(const float3 &c000, const float3 &c100, const float3 &c010, const float3 &c110,
+                                        const float3 &c001, const float3 &c101, const float3 &c011, const float3 &c111,
+                                        float fx, float fy, float fz)
 {
-    using O = Offsets<LAYOUT>;
-    const int x0 = O::ox(sx, F), x1 = O::ox(sx + 1, F);
-    const int y0 = O::oy(sy, F), y1 = O::oy(sy + 1, F);
-    const int z0 = O::oz(sz, F), z1 = O::oz(sz + 1, F);
-    const auto e000 = load_elem<DT>(brick + (z0 + y0 + x0));
-    const auto e100 = load_elem<DT>(brick + (z0 + y0 + x1));
-    const auto e010 = load_elem<DT>(brick + (z0 + y1 + x0));
-    const auto e110 = load_elem<DT>(brick + (z0 + y1 + x1));
-    const auto e001 = load_elem<DT>(brick + (z1 + y0 + x0));
-    const auto e101 = load_elem<DT>(brick + (z1 + y0 + x1));
-    const auto e011 = load_elem<DT>(brick + (z1 + y1 + x0));
-    const auto e111 = load_elem<DT>(brick + (z1 + y1 + x1));
-    const float3 c000 = decode_elem<DT>(e000), c100 = decode_elem<DT>(e100);
-    const float3 c010 = decode_elem<DT>(e010), c110 = decode_elem<DT>(e110);
-    const float3 c001 = decode_elem<DT>(e001), c101 = decode_elem<DT>(e101);
-    const float3 c011 = decode_elem<DT>(e011), c111 = decode_elem<DT>(e111);
     float3 r;
     r.x = lerpf(lerpf(lerpf(c000.x, c100.x, fx), lerpf(c010.x, c110.x, fx), fy),
                 lerpf(lerpf(c001.x, c101.x, fx), lerpf(c011.x, c111.x, fx), fy), fz);
@@ -227,6 +216,57 @@ __device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict
     r.z = lerpf(lerpf(lerpf(c000.z, c100.z, fx), lerpf(c010.z, c110.z, fx), fy),
                 lerpf(lerpf(c001.z, c101.z, fx), lerpf(c011.z, c111.z, fx), fy), fz);
     return r;
+}
+
+// Eight corner samples of one cell record (CELL8 layout): 4 x 16-byte loads
+// for 8-byte samples, 8 x 16-byte loads for FP32.
+template <int DT>
+__device__ __forceinline__ float3 trilerp_record(const typename Elem<DT>::T *__restrict__ rec, float fx, float fy,
+                                                 float fz)
+{
+    if constexpr (DT == SG_F32) {
+        const float4 *r = reinterpret_cast<const float4 *>(rec);
+        const float4 a0 = __ldg(r), a1 = __ldg(r + 1), a2 = __ldg(r + 2), a3 = __ldg(r + 3);
+        const float4 a4 = __ldg(r + 4), a5 = __ldg(r + 5), a6 = __ldg(r + 6), a7 = __ldg(r + 7);
+        return lerp8(decode_elem<DT>(a0), decode_elem<DT>(a1), decode_elem<DT>(a2), decode_elem<DT>(a3),
+                     decode_elem<DT>(a4), decode_elem<DT>(a5), decode_elem<DT>(a6), decode_elem<DT>(a7), fx, fy, fz);
+    } else {
+        const uint4 *r = reinterpret_cast<const uint4 *>(rec);
+        const uint4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
+        return lerp8(decode_elem<DT>(make_uint2(a.x, a.y)), decode_elem<DT>(make_uint2(a.z, a.w)),
+                     decode_elem<DT>(make_uint2(b.x, b.y)), decode_elem<DT>(make_uint2(b.z, b.w)),
+                     decode_elem<DT>(make_uint2(c.x, c.y)), decode_elem<DT>(make_uint2(c.z, c.w)),
+                     decode_elem<DT>(make_uint2(d.x, d.y)), decode_elem<DT>(make_uint2(d.z, d.w)), fx, fy, fz);
+    }
+}
+
+// Trilinear interpolation inside one brick: (sx, sy, sz) is the storage index
+// of the lower corner (for CELL8: the cell index), (fx, fy, fz) the fractions.
+// Returns the value before the brick scale (multiply by it for world units).
+template <int DT, int LAYOUT>
+__device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict__ brick, const DevField &F,
+                                          int sx, int sy, int sz, float fx, float fy, float fz)
+{
+    if constexpr (LAYOUT == SG_LAYOUT_CELL8) {
+        const int cell = (sz * F.C[1] + sy) * F.C[0] + sx;
+        return trilerp_record<DT>(brick + (long long)cell * 8, fx, fy, fz);
+    } else {
+        using O = Offsets<LAYOUT>;
+        const int x0 = O::ox(sx, F), x1 = O::ox(sx + 1, F);
+        const int y0 = O::oy(sy, F), y1 = O::oy(sy + 1, F);
+        const int z0 = O::oz(sz, F), z1 = O::oz(sz + 1, F);
+        const auto e000 = load_elem<DT>(brick + (z0 + y0 + x0));
+        const auto e100 = load_elem<DT>(brick + (z0 + y0 + x1));
+        const auto e010 = load_elem<DT>(brick + (z0 + y1 + x0));
+        const auto e110 = load_elem<DT>(brick + (z0 + y1 + x1));
+        const auto e001 = load_elem<DT>(brick + (z1 + y0 + x0));
+        const auto e101 = load_elem<DT>(brick + (z1 + y0 + x1));
+        const auto e011 = load_elem<DT>(brick + (z1 + y1 + x0));
+        const auto e111 = load_elem<DT>(brick + (z1 + y1 + x1));
+        return lerp8(decode_elem<DT>(e000), decode_elem<DT>(e100), decode_elem<DT>(e010), decode_elem<DT>(e110),
+                     decode_elem<DT>(e001), decode_elem<DT>(e101), decode_elem<DT>(e011), decode_elem<DT>(e111), fx,
+                     fy, fz);
+    }
 }
 
 // Not finite in any component (NaN or inf).  The sum of magnitudes is finite

@@ -130,9 +130,24 @@ __global__ void brick_store_kernel(StoreArgs A, int layout)
 {
     const DevField &F = A.F;
     const int b = A.brick0 + blockIdx.y;
-    const long long total = (long long)F.S[0] * F.S[1] * F.S[2];
     char *brick = A.data + (long long)b * A.brick_bytes;
     const float s = (DT == SG_F32) ? 1.0f : A.scales[b];
+    if (layout == SG_LAYOUT_CELL8) {
+        // one thread per stored element: cell record r >> 3, corner r & 7
+        const long long total = F.brick_elems;
+        for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total;
+             r += (long long)gridDim.x * blockDim.x) {
+            const long long cell = r >> 3;
+            const int corner = (int)(r & 7);
+            const int cx = (int)(cell % F.C[0]);
+            const int cy = (int)((cell / F.C[0]) % F.C[1]);
+            const int cz = (int)(cell / ((long long)F.C[0] * F.C[1]));
+            const float *src = src_sample(A, b, cx + (corner & 1), cy + ((corner >> 1) & 1), cz + (corner >> 2));
+            store_elem<DT>(brick, r, src[0], src[1], src[2], 0.0f, s);
+        }
+        return;
+    }
+    const long long total = (long long)F.S[0] * F.S[1] * F.S[2];
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total;
          r += (long long)gridDim.x * blockDim.x) {
         const int sx = (int)(r % F.S[0]);
@@ -218,7 +233,7 @@ sg_status launch_brick_store(sg_field *f, int slot, const float *src, int src_mo
     const int b0 = src_mode == 1 ? brick_index : 0;
     const int nbr = src_mode == 1 ? 1 : f->nb;
     A.brick0 = b0;
-    const long long total = (long long)A.F.S[0] * A.F.S[1] * A.F.S[2];
+    const long long total = d.layout == SG_LAYOUT_CELL8 ? A.F.brick_elems : (long long)A.F.S[0] * A.F.S[1] * A.F.S[2];
     const int block = 256;
     dim3 grid(grid_x_for(total, block, nbr, f->ctx->sm_count), nbr);
     if (d.dtype != SG_F32) {
@@ -289,7 +304,8 @@ static sg_status field_layout(const sg_field_desc *d, sg_field *f, size_t *bytes
     SG_CHECK(d->n_slots >= 1 && d->n_slots <= 64, SG_ERR_INVALID_ARG, "n_slots must be in [1, 64]");
     SG_CHECK(d->dtype == SG_F32 || d->dtype == SG_BF16 || d->dtype == SG_F16, SG_ERR_INVALID_ARG, "bad dtype %d",
              d->dtype);
-    SG_CHECK(d->layout == SG_LAYOUT_LINEAR || d->layout == SG_LAYOUT_TILED4 || d->layout == SG_FIELD_GLOBAL,
+    SG_CHECK(d->layout == SG_LAYOUT_LINEAR || d->layout == SG_LAYOUT_TILED4 || d->layout == SG_LAYOUT_CELL8 ||
+                 d->layout == SG_FIELD_GLOBAL,
              SG_ERR_INVALID_ARG, "bad layout %d", d->layout);
     SG_CHECK(d->n_slots == 1 || d->slice_dt > 0.0, SG_ERR_INVALID_ARG, "slice_dt must be > 0 for unsteady fields");
     DevField g;
@@ -324,11 +340,13 @@ static sg_status field_layout(const sg_field_desc *d, sg_field *f, size_t *bytes
             g.B[a] = d->bricks[a];
             g.S[a] = (int)n + 3;
             g.T[a] = (g.S[a] + 3) / 4;
+            g.C[a] = (int)n + 2;
             nb *= d->bricks[a];
         }
         elem = d->dtype == SG_F32 ? 16 : 8;
-        g.brick_elems = d->layout == SG_LAYOUT_LINEAR ? (long long)g.S[0] * g.S[1] * g.S[2]
-                                                      : (long long)g.T[0] * g.T[1] * g.T[2] * 64;
+        if (d->layout == SG_LAYOUT_LINEAR) g.brick_elems = (long long)g.S[0] * g.S[1] * g.S[2];
+        else if (d->layout == SG_LAYOUT_TILED4) g.brick_elems = (long long)g.T[0] * g.T[1] * g.T[2] * 64;
+        else g.brick_elems = (long long)g.C[0] * g.C[1] * g.C[2] * 8;
         SG_CHECK(g.brick_elems < (1ll << 31) - 1, SG_ERR_UNSUPPORTED, "a brick holds more than 2^31 samples");
         SG_CHECK(nb <= 65535, SG_ERR_UNSUPPORTED, "more than 65535 bricks");
         brick_bytes = align_up((size_t)g.brick_elems * elem, 256);

@@ -46,8 +46,9 @@ __device__ __forceinline__ float3 sample_slot(const DevField &F, const char *dat
     const int id = (b[2] * F.B[1] + b[1]) * F.B[0] + b[0];
     const T *brick = reinterpret_cast<const T *>(data) + (long long)id * F.brick_stride;
     const int sx = q[0] - lo[0] + 1, sy = q[1] - lo[1] + 1, sz = q[2] - lo[2] + 1;
-    float3 v = layout == SG_LAYOUT_LINEAR ? trilerp<DT, SG_LAYOUT_LINEAR>(brick, F, sx, sy, sz, g[0], g[1], g[2])
-                                          : trilerp<DT, SG_LAYOUT_TILED4>(brick, F, sx, sy, sz, g[0], g[1], g[2]);
+    float3 v = layout == SG_LAYOUT_LINEAR  ? trilerp<DT, SG_LAYOUT_LINEAR>(brick, F, sx, sy, sz, g[0], g[1], g[2])
+               : layout == SG_LAYOUT_CELL8 ? trilerp<DT, SG_LAYOUT_CELL8>(brick, F, sx, sy, sz, g[0], g[1], g[2])
+                                           : trilerp<DT, SG_LAYOUT_TILED4>(brick, F, sx, sy, sz, g[0], g[1], g[2]);
     if (DT != SG_F32) {
         const float s = __ldg(scales + id);
         v.x *= s;
@@ -348,12 +349,16 @@ sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaSt
         const double t0 = (double)(j - 1) * dt;
         const double times[3] = {t0, t0 + 0.5 * dt, t0 + dt};
         StreakParams P = streak_params(t);
+        int need[3][2];
         for (int st = 0; st < 3; ++st) {
             int sl;
             double al;
             slice_pair(times[st], sdt, &sl, &al);
+            // a slice with weight zero is not needed: sample the other one twice
+            need[st][0] = al == 1.0 ? sl + 1 : sl;
+            need[st][1] = al == 0.0 ? sl : sl + 1;
             for (int h = 0; h < 2; ++h) {
-                const int slice = sl + h;
+                const int slice = need[st][h];
                 const int slot = slice % f->desc.n_slots;
                 SG_CHECK(f->slot_slice[slot] == slice, SG_ERR_STATE,
                          "step %d needs time slice %d, which is not resident (slot %d holds %d)", j, slice, slot,
@@ -378,12 +383,7 @@ sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaSt
         }
         // later streams into these slots wait for this step
         for (int st = 0; st < 3; ++st)
-            for (int h = 0; h < 2; ++h) {
-                int sl;
-                double al;
-                slice_pair(times[st], sdt, &sl, &al);
-                SG_CUDA(cudaEventRecord(f->slot_used[(sl + h) % f->desc.n_slots], s));
-            }
+            for (int h = 0; h < 2; ++h) SG_CUDA(cudaEventRecord(f->slot_used[need[st][h] % f->desc.n_slots], s));
         if (j < t->p.inject_steps) t->births = j + 1;
         t->steps_done = j;
     }
