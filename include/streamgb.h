@@ -284,6 +284,37 @@ sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t *n_vertice
  * the particle-steps/s metric).  Synchronous. */
 sg_status sg_tracer_total_steps(sg_tracer *t, int64_t *steps, void *stream);
 
+/* ------------------------------------------------ allocation-free compaction */
+
+/* The paper has no counterpart to this call: it is a service for callers that
+ * must not allocate device memory, such as code running while a stream is
+ * captured in global mode (cudaMalloc is refused then), a simulation that has
+ * handed all of HBM to its own pool and lends its buffers to the field-line
+ * pass in situ, or a loop that cannot take the device-wide synchronisation
+ * that cudaMalloc/cudaFree may cause.
+ *
+ * Compacts per-line vertex slabs into CSR, as sg_tracer_get_lines does, but
+ * its scan scratch lives in a fixed array inside the library's device memory
+ * (32 KB on every GPU that loads the library, held until the process exits),
+ * so it calls no cudaMalloc, cudaFree or allocating routine.
+ *   slab      device, n_lines x max_vertices_per_line x 3 floats (line i's
+ *             vertices start at slab + 3 * i * max_vertices_per_line)
+ *   lengths   device, n_lines uint32 vertex counts, each <= max_vertices_per_line
+ *             (larger values are not checked and read past the slab)
+ *   offsets   out, n_lines + 1 int64 (device or page-locked host):
+ *             offsets[i] = sum of lengths before i, offsets[n_lines] = total
+ *   vertices  out, 3 * total floats (device or page-locked host), or NULL to
+ *             compute only the offsets
+ * n_lines above 16,777,216 (4096 chunks of 4096 lines), or
+ * max_vertices_per_line of 2^28 or more, is rejected with SG_ERR_INVALID_ARG.  The first call on a device looks up the scratch
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls on a device share the
+ * one scratch array and it keeps the last call's contents: calls that overlap
+ * on the GPU (different streams, or graphs launched concurrently) race and
+ * must be ordered by the caller.  Asynchronous on `stream`. */
+sg_status sg_lines_compact_static(const float *slab, int64_t max_vertices_per_line, const uint32_t *lengths,
+                                  int64_t n_lines, int64_t *offsets, float *vertices, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ SIGNATURES = {
     "sg_tracer_trace_timed": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), P], i32),
     "sg_tracer_get_lines": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P, P, P], i32),
     "sg_tracer_total_steps": ([P, ctypes.POINTER(i64), P], i32),
+    "sg_lines_compact_static": ([P, i64, P, i64, P, P, P], i32),
 }
 
 _lock = threading.Lock()

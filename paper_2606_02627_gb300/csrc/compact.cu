@@ -5,6 +5,8 @@
 // writes its vertex without any allocation.  Readback scans the line lengths
 // (exclusive scan to int64 offsets) and gathers every line's vertices to its
 // offset; the destination may be device or page-locked host memory.
+#include <mutex>
+
 #include "tracer.cuh"
 
 namespace sg {
@@ -165,4 +167,78 @@ sg_status launch_gather_lines(sg_tracer *t, int64_t *offsets, float *vertices, u
     return SG_OK;
 }
 
+// ------------------------------------------------------------------ allocation-free compaction
+//
+// Scratch of sg_lines_compact_static: one 64-bit sum per chunk of SCAN_CHUNK
+// lines plus the totals written by the middle scan pass.  It lives in the
+// library's own device memory (a file-scope array every GPU that loads the
+// library holds until the process exits), so the entry point needs no
+// allocation.  Every entry the scan reads is written earlier in the same call,
+// so nothing has to start at zero.
+constexpr long long STATIC_MAX_CHUNKS = 4096;
+constexpr long long STATIC_MAX_LINES = STATIC_MAX_CHUNKS * SCAN_CHUNK;   // 16,777,216 lines
+static __device__ __align__(256) unsigned long long g_compact_scratch[STATIC_MAX_CHUNKS + 8];
+
+// Host code may not use the array's name as a device address: its device
+// address is looked up once per device, with that device current.
+static std::mutex g_scratch_mu;
+static unsigned long long *g_scratch_dev[1024];
+
+static sg_status static_scratch(unsigned long long **out)
+{
+    int dev = 0;
+    SG_CUDA(cudaGetDevice(&dev));
+    SG_CHECK(dev >= 0 && dev < 1024, SG_ERR_UNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+        void *p = nullptr;
+        SG_CUDA(cudaGetSymbolAddress(&p, g_compact_scratch));
+        g_scratch_dev[dev] = (unsigned long long *)p;
+    }
+    *out = g_scratch_dev[dev];
+    return SG_OK;
+}
+
 }  // namespace sg
+
+using namespace sg;
+
+extern "C" sg_status sg_lines_compact_static(const float *slab, int64_t max_vertices_per_line, const uint32_t *lengths,
+                                             int64_t n_lines, int64_t *offsets, float *vertices, void *stream)
+{
+    SG_CHECK(n_lines >= 0, SG_ERR_INVALID_ARG, "n_lines must be >= 0");
+    SG_CHECK(n_lines <= STATIC_MAX_LINES, SG_ERR_INVALID_ARG,
+             "n_lines = %lld exceeds the limit of the allocation-free compaction (%lld lines)", (long long)n_lines,
+             (long long)STATIC_MAX_LINES);
+    SG_CHECK(max_vertices_per_line >= 1 && max_vertices_per_line < (1ll << 28), SG_ERR_INVALID_ARG,
+             "max_vertices_per_line must be in [1, 2^28)");
+    SG_CHECK(offsets != nullptr, SG_ERR_INVALID_ARG, "offsets is NULL");
+    SG_CHECK(n_lines == 0 || (lengths != nullptr && (slab != nullptr || vertices == nullptr)), SG_ERR_INVALID_ARG,
+             "NULL input");
+    unsigned long long *scratch = nullptr;
+    sg_status st = static_scratch(&scratch);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = n_lines;
+    const long long nblocks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    int64_t *totals = reinterpret_cast<int64_t *>(scratch + STATIC_MAX_CHUNKS);
+    if (nblocks > 0) {
+        scan_reduce_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(lengths, n, scratch);
+        SG_CUDA(cudaGetLastError());
+    }
+    scan_blocks_kernel<<<1, SCAN_THREADS, 0, s>>>(scratch, nblocks, totals, offsets, n);
+    SG_CUDA(cudaGetLastError());
+    if (nblocks > 0) {
+        scan_apply_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(lengths, n, scratch, offsets);
+        SG_CUDA(cudaGetLastError());
+        if (vertices) {
+            int dev = 0, sms = 0;
+            SG_CUDA(cudaGetDevice(&dev));
+            SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            gather_lines_kernel<<<sms * 8, 256, 0, s>>>(slab, (long long)max_vertices_per_line, lengths, offsets, n,
+                                                        vertices, nullptr, nullptr, nullptr, nullptr, nullptr);
+            SG_CUDA(cudaGetLastError());
+        }
+    }
+    return SG_OK;
+}
