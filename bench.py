@@ -9,8 +9,11 @@ one-cell ghost shell and encoded to the benchmarked storage type; 1M seeds
 with h = 0.5 cell runs to max 2000 steps (exit / |v| < 1e-6 / cap) with
 cross-brick hand-off queues; the lines are compacted to CSR.
 
-`value` is the BF16-field persistent form (the precision form); the FP32
-persistent form, the plain FP32 per-seed kernel and (optionally) the
+`value` is the persistent form on the 16-bit-footprint precision field: 21-bit
+fixed point, three components in the 8 bytes a BF16 sample takes, per-brick
+scale (the BF16 and FP16 fields are as fast but their 8- and 11-bit mantissas
+miss the 5e-2-cell error bound on this flow).  The BF16, FP16 and FP32
+persistent forms, the plain FP32 per-seed kernel and (optionally) the
 one-launch-per-step kernel of Listing 1 are timed in the same run under
 `variants`.  `e2e` repeats the headline through the C ABI with the seeds
 copied from page-locked host memory and the CSR lines written to page-locked
@@ -36,7 +39,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-GATHER_BYTES = {"f32": 4 * 8 * 3 * 4 + 12, "bf16": 4 * 8 * 3 * 2 + 12, "f16": 4 * 8 * 3 * 2 + 12}
+# algorithmic bytes per particle-step: 4 samples x 8 corners x 3 components x element bytes + a 12-B vertex
+# (FX21 packs 3 components in 8 bytes: 8/3 bytes per component, the same 64 bits per corner as BF16x4)
+GATHER_BYTES = {"f32": 4 * 8 * 3 * 4 + 12, "bf16": 4 * 8 * 3 * 2 + 12, "f16": 4 * 8 * 3 * 2 + 12,
+                "fx21": 4 * 8 * 8 + 12}
 METRIC = "RK4 particle-steps/s"
 UNIT = "particle-steps/s"
 
@@ -51,8 +57,8 @@ def parse():
     ap.add_argument("--seeds", type=int, default=1 << 20)
     ap.add_argument("--max-steps", type=int, default=2000)
     ap.add_argument("--h", type=float, default=0.5)
-    ap.add_argument("--dtype", default="bf16", choices=["f32", "bf16", "f16"])
-    ap.add_argument("--layout", default="linear")
+    ap.add_argument("--dtype", default="fx21", choices=["f32", "bf16", "f16", "fx21"])
+    ap.add_argument("--layout", default="cell8")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--per-step", action="store_true", help="also time the one-launch-per-step kernel")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
@@ -313,7 +319,7 @@ def main():
     except Exception:
         pass
 
-    # headline: BF16 (or the chosen storage) persistent form
+    # headline: the chosen storage type, persistent form
     fld, tr = make(args.dtype, args.layout, "persistent")
     with Clocks(uuid) as clk:
         ms, tot, tot_all, _ = timed(fld, tr, args.warmup, args.steps, seeds_dev)
@@ -347,9 +353,9 @@ def main():
 
     variants = {}
     if not args.no_variants:
-        runs = [("f32_persistent", "f32", args.layout, "persistent"), ("f32_per_seed", "f32", "global", "per_seed")]
-        if args.dtype != "bf16":
-            runs.insert(0, ("bf16_persistent", "bf16", args.layout, "persistent"))
+        runs = [(f"{d}_persistent", d, args.layout, "persistent") for d in ("fx21", "f16", "bf16", "f32")
+                if d != args.dtype]
+        runs.append(("f32_per_seed", "f32", "global", "per_seed"))
         if args.per_step:
             runs.append(("f32_per_step", "f32", args.layout, "per_step"))
         for name, dtp, lay, ker in runs:

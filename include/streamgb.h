@@ -57,8 +57,15 @@ enum {
  * store code = round-to-nearest-even(v / s_b) with one scale s_b per brick,
  * s_b the smallest power of two >= the largest finite |component| among the
  * brick's stored samples (ghosts included), and decode as code * s_b.
- * Interpolation and integration are FP32 in every case. */
-enum { SG_F32 = 0, SG_BF16 = 1, SG_F16 = 2 };
+ * SG_FX21 stores the three components as 21-bit signed fixed-point integers
+ * q = round-to-nearest-even(v / s_b * 2^20), clamped to +-(2^20 - 1), packed
+ * with a non-finite flag in the same 8 bytes a BF16 sample takes (x: bits
+ * 0-20, y: bits 21-41, flag: bit 42, z: bits 43-63, each as q + 2^20); it
+ * decodes as q * s_b * 2^-20 (the per-brick scale it reports is that quantum),
+ * an absolute error of at most s_b * 2^-21, and a sample with a non-finite
+ * component decodes as NaN.  Interpolation and integration are FP32 in every
+ * case. */
+enum { SG_F32 = 0, SG_BF16 = 1, SG_F16 = 2, SG_FX21 = 3 };
 
 /* Sample layout inside a brick.  A sample is x, y, z and one pad: 16 B in
  * FP32, 8 B in BF16/FP16.  LINEAR is x-fastest; TILED4 groups 4x4x4 samples
@@ -188,10 +195,11 @@ sg_status sg_field_stream_slice(sg_field *f, int32_t slice, const float *pinned_
  * Synchronous on `stream`. */
 sg_status sg_field_max_speed(sg_field *f, int32_t slot, double *cells_per_time, void *stream);
 
-/* Copies brick (bx,by,bz) of `slot` back in a canonical form: FP32 stores give
- * (n+3)^3*3 floats, BF16/FP16 stores give (n+3)^3*3 uint16 codes (z, y, x,
- * component order) and the brick scale.  `out` is host memory of at least
- * (n+3)^3*3*(4 or 2) bytes.  Synchronous. */
+/* Copies brick (bx,by,bz) of `slot` back in a canonical form (z, y, x,
+ * component order): FP32 stores give (n+3)^3*3 floats, BF16/FP16 stores
+ * (n+3)^3*3 uint16 codes, FX21 stores (n+3)^3*3 int32 codes q (INT32_MIN in
+ * every component of a sample flagged non-finite), and the brick scale.
+ * `out` is host memory of at least (n+3)^3*3*(4, 2 or 4) bytes.  Synchronous. */
 sg_status sg_field_read_brick(sg_field *f, int32_t slot, int32_t bx, int32_t by, int32_t bz,
                               void *out, float *scale, void *stream);
 

@@ -21,9 +21,10 @@
  *  - trace(): steps until the step cap is met or the particle stops (Sec. 3.2).
  *  - streaklines (Sec. 3.2, Listing 2): one new particle per release point per
  *    step, the field linear in time between stored slices.
- *  - the per-brick quantisation of the stored field (BF16 / FP16 codes and a
- *    per-brick power-of-two scale), which the paper does not have; it is the
- *    precision form of the field store, restated here from its definition.
+ *  - the per-brick quantisation of the stored field (BF16 / FP16 codes, or
+ *    21-bit fixed-point codes, and a per-brick power-of-two scale), which the
+ *    paper does not have; it is the precision form of the field store,
+ *    restated here from its definition.
  *
  * Readings where the paper is silent (each is also stated where it is used):
  *  - positions are in index space (cells); world = origin + spacing * index;
@@ -63,6 +64,7 @@
 #define OR_F32 0
 #define OR_BF16 1
 #define OR_F16 2
+#define OR_FX21 3
 
 int or_version(void) { return 1; }
 
@@ -478,18 +480,34 @@ static float pow2_ceil(float m)
 
 static int64_t clampi(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* 21-bit fixed point: q = round-to-nearest-even(r * 2^20) with r = v / s_b,
+ * clamped to +-(2^20 - 1).  Decodes as q * s_b * 2^-20. */
+static int32_t fx21_q(float r)
+{
+    double q = nearbyint((double)r * 1048576.0);
+    if (q > 1048575.0) q = 1048575.0;
+    if (q < -1048575.0) q = -1048575.0;
+    return (int32_t)q;
+}
+
 /* Quantise the global FP32 field into bricks.
- *   scales: nbricks floats (brick order x fastest), may be NULL;
- *   codes:  nbricks * (n+3)^3 * 3 uint16 (brick-major, then z, y, x, comp), may be NULL;
+ *   scales: nbricks floats (brick order x fastest), may be NULL; for OR_FX21
+ *           the scale is the quantum s_b * 2^-20;
+ *   codes:  nbricks * (n+3)^3 * 3 codes (brick-major, then z, y, x, comp), may
+ *           be NULL: uint16 for BF16/FP16, int32 q for FX21 (INT32_MIN in all
+ *           three components of a sample with a non-finite component);
  *   dequant: N^3 * 3 floats, each sample decoded with its owning brick's scale
- *            (exactly representable in float), may be NULL.
+ *            (exactly representable in float), may be NULL; for FX21 a sample
+ *            with a non-finite component decodes as NaN in all components.
  * dtype OR_F32 gives scales of 1, no codes, dequant = input. */
 int or_quantize_field(const float *F, const int64_t dims[3], const int32_t bricks[3], int dtype,
-                      float *scales, uint16_t *codes, float *dequant)
+                      float *scales, void *codes_out, float *dequant)
 {
+    uint16_t *codes = (uint16_t *)codes_out;
+    int32_t *qcodes = (int32_t *)codes_out;
     int64_t n[3];
     if (or_brick_cells(dims, bricks, n)) return -1;
-    if (dtype != OR_F32 && dtype != OR_BF16 && dtype != OR_F16) return -1;
+    if (dtype != OR_F32 && dtype != OR_BF16 && dtype != OR_F16 && dtype != OR_FX21) return -1;
     int64_t nb = (int64_t)bricks[0] * bricks[1] * bricks[2];
     float *sc = (float *)malloc(sizeof(float) * (size_t)nb);
     if (!sc) return -2;
@@ -510,8 +528,21 @@ int or_quantize_field(const float *F, const int64_t dims[3], const int32_t brick
                     }
                 }
         sc[b] = dtype == OR_F32 ? 1.0f : pow2_ceil(m);
-        if (scales) scales[b] = sc[b];
-        if (codes && dtype != OR_F32) {
+        if (scales) scales[b] = dtype == OR_FX21 ? sc[b] / 1048576.0f : sc[b];
+        if (codes_out && dtype == OR_FX21) {
+            int32_t *cb = qcodes + b * S[0] * S[1] * S[2] * 3;
+            for (int64_t sz = 0; sz < S[2]; ++sz)
+                for (int64_t sy = 0; sy < S[1]; ++sy)
+                    for (int64_t sx = 0; sx < S[0]; ++sx) {
+                        int64_t gx = clampi(bx * n[0] - 1 + sx, 0, dims[0] - 1);
+                        int64_t gy = clampi(by * n[1] - 1 + sy, 0, dims[1] - 1);
+                        int64_t gz = clampi(bz * n[2] - 1 + sz, 0, dims[2] - 1);
+                        const float *smp = F + 3 * ((gz * dims[1] + gy) * dims[0] + gx);
+                        int32_t *o = cb + ((sz * S[1] + sy) * S[0] + sx) * 3;
+                        int bad = !(isfinite(smp[0]) && isfinite(smp[1]) && isfinite(smp[2]));
+                        for (int c = 0; c < 3; ++c) o[c] = bad ? INT32_MIN : fx21_q(smp[c] / sc[b]);
+                    }
+        } else if (codes_out && dtype != OR_F32) {
             uint16_t *cb = codes + b * S[0] * S[1] * S[2] * 3;
             for (int64_t sz = 0; sz < S[2]; ++sz)
                 for (int64_t sy = 0; sy < S[1]; ++sy)
@@ -539,6 +570,12 @@ int or_quantize_field(const float *F, const int64_t dims[3], const int32_t brick
                     int64_t bz = clampi(gz / n[2], 0, bricks[2] - 1);
                     float s_b = sc[(bz * bricks[1] + by) * bricks[0] + bx];
                     int64_t i = 3 * ((gz * dims[1] + gy) * dims[0] + gx);
+                    if (dtype == OR_FX21) {
+                        int bad = !(isfinite(F[i]) && isfinite(F[i + 1]) && isfinite(F[i + 2]));
+                        for (int c = 0; c < 3; ++c)
+                            dequant[i + c] = bad ? NAN : (float)((double)fx21_q(F[i + c] / s_b) * (double)s_b / 1048576.0);
+                        continue;
+                    }
                     for (int c = 0; c < 3; ++c) {
                         if (dtype == OR_F32) { dequant[i + c] = F[i + c]; continue; }
                         float r = isfinite(F[i + c]) ? F[i + c] / s_b : NAN;

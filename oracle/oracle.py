@@ -24,7 +24,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 ACTIVE, MAXSTEPS, EXIT, STAGNANT, NANFIELD, OUT = 0, 1, 2, 3, 4, 5
 NOT_RELEASED = 255
 # storage types
-F32, BF16, F16 = 0, 1, 2
+F32, BF16, F16, FX21 = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -203,8 +203,9 @@ def owner_brick(dims, bricks, p_index):
 
 
 def quantize_field(F, bricks, dtype, want_codes=False, want_dequant=True):
-    """Per-brick scales, optional per-brick codes ((nb, S, S, S, 3) uint16) and the
-    dequantised global field (float32, each sample with its owning brick's scale)."""
+    """Per-brick scales, optional per-brick codes ((nb, S, S, S, 3) uint16, or int32
+    for FX21) and the dequantised global field (float32, each sample with its
+    owning brick's scale)."""
     lib = _load()
     F, dims = _field(F)
     b = np.ascontiguousarray(bricks, dtype=np.int32)
@@ -213,7 +214,7 @@ def quantize_field(F, bricks, dtype, want_codes=False, want_dequant=True):
     scales = np.zeros(nb, dtype=np.float32)
     codes = None
     if want_codes and dtype != F32:
-        codes = np.zeros((nb, n[2] + 3, n[1] + 3, n[0] + 3, 3), dtype=np.uint16)
+        codes = np.zeros((nb, n[2] + 3, n[1] + 3, n[0] + 3, 3), dtype=np.int32 if dtype == FX21 else np.uint16)
     deq = np.zeros_like(F) if want_dequant else None
     rc = lib.or_quantize_field(_p(F), _p(dims), _p(b), int(dtype), _p(scales),
                                _p(codes) if codes is not None else None,

@@ -25,7 +25,7 @@ SG_ERR_UNSUPPORTED = -7
 ERR_NAMES = {0: "SG_OK", -1: "SG_ERR_INVALID_ARG", -2: "SG_ERR_OOM", -3: "SG_ERR_CUDA",
              -4: "SG_ERR_ROUND_LIMIT", -5: "SG_ERR_TIMEOUT", -6: "SG_ERR_STATE", -7: "SG_ERR_UNSUPPORTED"}
 
-SG_F32, SG_BF16, SG_F16 = 0, 1, 2
+SG_F32, SG_BF16, SG_F16, SG_FX21 = 0, 1, 2, 3
 SG_LAYOUT_LINEAR, SG_LAYOUT_TILED4, SG_LAYOUT_CELL8, SG_FIELD_GLOBAL = 0, 1, 2, 16
 SG_STREAMLINE, SG_STREAKLINE = 0, 1
 SG_KERNEL_PERSISTENT, SG_KERNEL_PER_SEED, SG_KERNEL_PER_STEP = 0, 1, 2

@@ -14,7 +14,7 @@ import torch
 from . import _lib as L
 from ._lib import call
 
-DTYPES = {"f32": L.SG_F32, "bf16": L.SG_BF16, "f16": L.SG_F16}
+DTYPES = {"f32": L.SG_F32, "bf16": L.SG_BF16, "f16": L.SG_F16, "fx21": L.SG_FX21}
 LAYOUTS = {"linear": L.SG_LAYOUT_LINEAR, "tiled4": L.SG_LAYOUT_TILED4, "cell8": L.SG_LAYOUT_CELL8,
            "global": L.SG_FIELD_GLOBAL}
 KERNELS = {"persistent": L.SG_KERNEL_PERSISTENT, "per_seed": L.SG_KERNEL_PER_SEED, "per_step": L.SG_KERNEL_PER_STEP}
@@ -119,7 +119,7 @@ class Field:
     def read_brick(self, bx, by, bz, slot: int = 0, stream=None):
         n = self.brick_cells()
         shape = (n[2] + 3, n[1] + 3, n[0] + 3, 3)
-        out = np.zeros(shape, dtype=np.float32 if self.desc.dtype == L.SG_F32 else np.uint16)
+        out = np.zeros(shape, dtype={L.SG_F32: np.float32, L.SG_FX21: np.int32}.get(self.desc.dtype, np.uint16))
         sc = ctypes.c_float()
         call("sg_field_read_brick", self.h, slot, bx, by, bz, _ptr(out), ctypes.byref(sc), _stream(stream))
         return out, sc.value

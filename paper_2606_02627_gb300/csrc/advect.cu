@@ -528,21 +528,15 @@ static void launch_round_t(const LineParams &P, int grid, int block, int kernel,
 sg_status launch_round(sg_tracer *t, cudaStream_t s)
 {
     LineParams P = line_params(t);
-    const int dt = t->field->desc.dtype, lay = t->field->desc.layout;
     const int k = t->p.kernel;
-    if (lay == SG_LAYOUT_CELL8) {
-        if (dt == SG_F32) launch_round_t<SG_F32, SG_LAYOUT_CELL8>(P, t->grid, t->block, k, s);
-        else if (dt == SG_BF16) launch_round_t<SG_BF16, SG_LAYOUT_CELL8>(P, t->grid, t->block, k, s);
-        else launch_round_t<SG_F16, SG_LAYOUT_CELL8>(P, t->grid, t->block, k, s);
-    } else if (lay == SG_LAYOUT_LINEAR) {
-        if (dt == SG_F32) launch_round_t<SG_F32, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);
-        else if (dt == SG_BF16) launch_round_t<SG_BF16, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);
-        else launch_round_t<SG_F16, SG_LAYOUT_LINEAR>(P, t->grid, t->block, k, s);
-    } else {
-        if (dt == SG_F32) launch_round_t<SG_F32, SG_LAYOUT_TILED4>(P, t->grid, t->block, k, s);
-        else if (dt == SG_BF16) launch_round_t<SG_BF16, SG_LAYOUT_TILED4>(P, t->grid, t->block, k, s);
-        else launch_round_t<SG_F16, SG_LAYOUT_TILED4>(P, t->grid, t->block, k, s);
-    }
+    bool ok = false;
+    with_dtype(t->field->desc.dtype, [&](auto D) {
+        ok = with_layout(t->field->desc.layout, [&](auto Lay) {
+            launch_round_t<decltype(D)::value, decltype(Lay)::value>(P, t->grid, t->block, k, s);
+        });
+    });
+    SG_CHECK(ok, SG_ERR_UNSUPPORTED, "no advection kernel for dtype %d layout %d", t->field->desc.dtype,
+             t->field->desc.layout);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }

@@ -19,6 +19,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <type_traits>
+
 #include "streamgb.h"
 
 #define SG_FULL_MASK 0xffffffffu
@@ -140,6 +142,31 @@ template <int DT> struct Elem;
 template <> struct Elem<SG_F32> { using T = float4; };
 template <> struct Elem<SG_BF16> { using T = uint2; };
 template <> struct Elem<SG_F16> { using T = uint2; };
+template <> struct Elem<SG_FX21> { using T = uint2; };
+
+// Dispatch on the storage type: fn(std::integral_constant<int, DT>{}).
+template <class Fn>
+inline bool with_dtype(int dt, Fn &&fn)
+{
+    switch (dt) {
+    case SG_F32: fn(std::integral_constant<int, SG_F32>{}); return true;
+    case SG_BF16: fn(std::integral_constant<int, SG_BF16>{}); return true;
+    case SG_F16: fn(std::integral_constant<int, SG_F16>{}); return true;
+    case SG_FX21: fn(std::integral_constant<int, SG_FX21>{}); return true;
+    default: return false;
+    }
+}
+
+template <class Fn>
+inline bool with_layout(int layout, Fn &&fn)
+{
+    switch (layout) {
+    case SG_LAYOUT_LINEAR: fn(std::integral_constant<int, SG_LAYOUT_LINEAR>{}); return true;
+    case SG_LAYOUT_TILED4: fn(std::integral_constant<int, SG_LAYOUT_TILED4>{}); return true;
+    case SG_LAYOUT_CELL8: fn(std::integral_constant<int, SG_LAYOUT_CELL8>{}); return true;
+    default: return false;
+    }
+}
 
 template <int DT>
 __device__ __forceinline__ float3 decode_elem(typename Elem<DT>::T v);
@@ -160,6 +187,29 @@ __device__ __forceinline__ float3 decode_elem<SG_F16>(uint2 v)
     float2 a = __half22float2(h);
     float z = __half2float(__ushort_as_half((unsigned short)(v.y & 0xffffu)));
     return make_float3(a.x, a.y, z);
+}
+
+// FX21: each component is q + 2^20 in 21 bits; OR-ing the exponent of 2^23
+// over the low 23 bits gives the float 2^23 + q + 2^20 exactly, and one
+// subtraction of 2^23 + 2^20 leaves q (no integer-to-float conversion).
+constexpr unsigned FX21_MASK = 0x1FFFFFu;
+constexpr unsigned FX21_FLAG = 0x400u;     // bit 42 of the sample = bit 10 of the high word
+__device__ __forceinline__ float fx21_value(unsigned u) { return __int_as_float(0x4B000000u | u) - 9437184.0f; }
+
+template <>
+__device__ __forceinline__ float3 decode_elem<SG_FX21>(uint2 v)
+{
+    return make_float3(fx21_value(v.x & FX21_MASK), fx21_value(__funnelshift_r(v.x, v.y, 21) & FX21_MASK),
+                       fx21_value(v.y >> 11));
+}
+
+// Non-finite flag of a stored sample (only FX21 has one; the float formats
+// carry NaN in the value itself).
+template <int DT>
+__device__ __forceinline__ unsigned elem_flag(typename Elem<DT>::T v)
+{
+    if constexpr (DT == SG_FX21) return v.y & FX21_FLAG;
+    else return 0u;
 }
 
 template <int DT>
@@ -233,10 +283,14 @@ __device__ __forceinline__ float3 trilerp_record(const typename Elem<DT>::T *__r
     } else {
         const uint4 *r = reinterpret_cast<const uint4 *>(rec);
         const uint4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
-        return lerp8(decode_elem<DT>(make_uint2(a.x, a.y)), decode_elem<DT>(make_uint2(a.z, a.w)),
-                     decode_elem<DT>(make_uint2(b.x, b.y)), decode_elem<DT>(make_uint2(b.z, b.w)),
-                     decode_elem<DT>(make_uint2(c.x, c.y)), decode_elem<DT>(make_uint2(c.z, c.w)),
-                     decode_elem<DT>(make_uint2(d.x, d.y)), decode_elem<DT>(make_uint2(d.z, d.w)), fx, fy, fz);
+        float3 v = lerp8(decode_elem<DT>(make_uint2(a.x, a.y)), decode_elem<DT>(make_uint2(a.z, a.w)),
+                         decode_elem<DT>(make_uint2(b.x, b.y)), decode_elem<DT>(make_uint2(b.z, b.w)),
+                         decode_elem<DT>(make_uint2(c.x, c.y)), decode_elem<DT>(make_uint2(c.z, c.w)),
+                         decode_elem<DT>(make_uint2(d.x, d.y)), decode_elem<DT>(make_uint2(d.z, d.w)), fx, fy, fz);
+        if constexpr (DT == SG_FX21) {
+            if ((a.y | a.w | b.y | b.w | c.y | c.w | d.y | d.w) & FX21_FLAG) v = make_float3(NAN, NAN, NAN);
+        }
+        return v;
     }
 }
 
@@ -263,9 +317,15 @@ __device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict
         const auto e101 = load_elem<DT>(brick + (z1 + y0 + x1));
         const auto e011 = load_elem<DT>(brick + (z1 + y1 + x0));
         const auto e111 = load_elem<DT>(brick + (z1 + y1 + x1));
-        return lerp8(decode_elem<DT>(e000), decode_elem<DT>(e100), decode_elem<DT>(e010), decode_elem<DT>(e110),
-                     decode_elem<DT>(e001), decode_elem<DT>(e101), decode_elem<DT>(e011), decode_elem<DT>(e111), fx,
-                     fy, fz);
+        float3 v = lerp8(decode_elem<DT>(e000), decode_elem<DT>(e100), decode_elem<DT>(e010), decode_elem<DT>(e110),
+                         decode_elem<DT>(e001), decode_elem<DT>(e101), decode_elem<DT>(e011), decode_elem<DT>(e111), fx,
+                         fy, fz);
+        if constexpr (DT == SG_FX21) {
+            if ((elem_flag<DT>(e000) | elem_flag<DT>(e100) | elem_flag<DT>(e010) | elem_flag<DT>(e110) |
+                 elem_flag<DT>(e001) | elem_flag<DT>(e101) | elem_flag<DT>(e011) | elem_flag<DT>(e111)))
+                v = make_float3(NAN, NAN, NAN);
+        }
+        return v;
     }
 }
 

@@ -82,11 +82,13 @@ __device__ __forceinline__ float pow2_ceil(float m)
     return fr == 0.5f ? m : ldexpf(1.0f, e);
 }
 
-__global__ void brick_scale_kernel(unsigned *maxbits, float *scales, int b0, int nb)
+// mult: 1 for the float formats; 2^-20 for FX21, whose stored scale is the
+// quantum s_b * 2^-20 (a power of two as well).
+__global__ void brick_scale_kernel(unsigned *maxbits, float *scales, int b0, int nb, float mult)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
-    scales[b0 + i] = pow2_ceil(__uint_as_float(maxbits[b0 + i]));
+    scales[b0 + i] = pow2_ceil(__uint_as_float(maxbits[b0 + i])) * mult;
     maxbits[b0 + i] = 0u;   // ready for the next store
 }
 
@@ -123,6 +125,33 @@ __device__ __forceinline__ void store_elem<SG_F16>(char *brick, long long idx, f
     const unsigned short hy = __half_as_ushort(__float2half_rn(scaled(y, s)));
     const unsigned short hz = __half_as_ushort(__float2half_rn(scaled(z, s)));
     reinterpret_cast<uint2 *>(brick)[idx] = make_uint2((unsigned)hx | ((unsigned)hy << 16), (unsigned)hz);
+}
+
+// FX21: q = round-to-nearest-even(v / quantum), clamped to +-(2^20 - 1), stored
+// as q + 2^20; the quotient by a power of two is exact.  A non-finite component
+// sets the sample's flag (and stores zero).
+__device__ __forceinline__ unsigned fx21_code(float v, float quantum, unsigned &flag)
+{
+    if (!(fabsf(v) < INFINITY)) {
+        flag = FX21_FLAG;
+        return 1u << 20;
+    }
+    int q = __float2int_rn(v / quantum);
+    q = max(-(1 << 20) + 1, min((1 << 20) - 1, q));
+    return (unsigned)(q + (1 << 20));
+}
+
+template <>
+__device__ __forceinline__ void store_elem<SG_FX21>(char *brick, long long idx, float x, float y, float z, float,
+                                                    float quantum)
+{
+    unsigned flag = 0;
+    const unsigned ux = fx21_code(x, quantum, flag);
+    const unsigned uy = fx21_code(y, quantum, flag);
+    const unsigned uz = fx21_code(z, quantum, flag);
+    const unsigned lo = ux | (uy << 21);
+    const unsigned hi = (uy >> 11) | flag | (uz << 11);
+    reinterpret_cast<uint2 *>(brick)[idx] = make_uint2(lo, hi);
 }
 
 template <int DT>
@@ -241,14 +270,11 @@ sg_status launch_brick_store(sg_field *f, int slot, const float *src, int src_mo
         SG_CUDA(cudaGetLastError());
     }
     // FP32 bricks leave the max-abs words at zero, which gives a scale of 1
-    brick_scale_kernel<<<(nbr + 255) / 256, 256, 0, s>>>(f->maxbits, A.scales, b0, nbr);
+    brick_scale_kernel<<<(nbr + 255) / 256, 256, 0, s>>>(f->maxbits, A.scales, b0, nbr,
+                                                         d.dtype == SG_FX21 ? 1.0f / 1048576.0f : 1.0f);
     SG_CUDA(cudaGetLastError());
-    switch (d.dtype) {
-    case SG_F32: brick_store_kernel<SG_F32><<<grid, block, 0, s>>>(A, d.layout); break;
-    case SG_BF16: brick_store_kernel<SG_BF16><<<grid, block, 0, s>>>(A, d.layout); break;
-    case SG_F16: brick_store_kernel<SG_F16><<<grid, block, 0, s>>>(A, d.layout); break;
-    default: SG_CHECK(false, SG_ERR_UNSUPPORTED, "unsupported dtype %d", d.dtype);
-    }
+    const bool ok = with_dtype(d.dtype, [&](auto D) { brick_store_kernel<decltype(D)::value><<<grid, block, 0, s>>>(A, d.layout); });
+    SG_CHECK(ok, SG_ERR_UNSUPPORTED, "unsupported dtype %d", d.dtype);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }
@@ -268,20 +294,10 @@ sg_status launch_max_speed(sg_field *f, int slot, cudaStream_t s)
     DevField F = field_view(f, slot);
     const int block = 256;
     dim3 grid(grid_x_for((long long)F.S[0] * F.S[1] * F.S[2], block, f->nb, f->ctx->sm_count), f->nb);
-    switch (d.dtype) {
-    case SG_F32:
-        max_speed_kernel<SG_F32><<<grid, block, 0, s>>>(F, (long long)f->brick_bytes, d.layout, isx, isy, isz,
-                                                        f->speed_bits);
-        break;
-    case SG_BF16:
-        max_speed_kernel<SG_BF16><<<grid, block, 0, s>>>(F, (long long)f->brick_bytes, d.layout, isx, isy, isz,
-                                                         f->speed_bits);
-        break;
-    default:
-        max_speed_kernel<SG_F16><<<grid, block, 0, s>>>(F, (long long)f->brick_bytes, d.layout, isx, isy, isz,
-                                                        f->speed_bits);
-        break;
-    }
+    with_dtype(d.dtype, [&](auto D) {
+        max_speed_kernel<decltype(D)::value><<<grid, block, 0, s>>>(F, (long long)f->brick_bytes, d.layout, isx, isy,
+                                                                     isz, f->speed_bits);
+    });
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }
@@ -302,8 +318,8 @@ static sg_status field_layout(const sg_field_desc *d, sg_field *f, size_t *bytes
         SG_CHECK(d->bricks[a] >= 1, SG_ERR_INVALID_ARG, "bricks[%d] must be >= 1", a);
     }
     SG_CHECK(d->n_slots >= 1 && d->n_slots <= 64, SG_ERR_INVALID_ARG, "n_slots must be in [1, 64]");
-    SG_CHECK(d->dtype == SG_F32 || d->dtype == SG_BF16 || d->dtype == SG_F16, SG_ERR_INVALID_ARG, "bad dtype %d",
-             d->dtype);
+    SG_CHECK(d->dtype == SG_F32 || d->dtype == SG_BF16 || d->dtype == SG_F16 || d->dtype == SG_FX21,
+             SG_ERR_INVALID_ARG, "bad dtype %d", d->dtype);
     SG_CHECK(d->layout == SG_LAYOUT_LINEAR || d->layout == SG_LAYOUT_TILED4 || d->layout == SG_LAYOUT_CELL8 ||
                  d->layout == SG_FIELD_GLOBAL,
              SG_ERR_INVALID_ARG, "bad layout %d", d->layout);
@@ -554,7 +570,6 @@ extern "C" sg_status sg_field_read_brick(sg_field *f, int32_t slot, int32_t bx, 
         free(raw);
         return cuda_error(e, "read_brick copy");
     }
-    if (f->desc.dtype == SG_F32) sc = 1.0f;
     if (scale) *scale = sc;
     for (int z = 0; z < g.S[2]; ++z)
         for (int y = 0; y < g.S[1]; ++y)
@@ -567,6 +582,14 @@ extern "C" sg_status sg_field_read_brick(sg_field *f, int32_t slot, int32_t bx, 
                     o[0] = v[0];
                     o[1] = v[1];
                     o[2] = v[2];
+                } else if (f->desc.dtype == SG_FX21) {
+                    const uint32_t *v = reinterpret_cast<const uint32_t *>(raw) + 2 * src;
+                    int32_t *o = reinterpret_cast<int32_t *>(out) + dst;
+                    const uint32_t lo = v[0], hi = v[1];
+                    const bool bad = (hi & 0x400u) != 0;
+                    o[0] = bad ? INT32_MIN : (int32_t)(lo & 0x1FFFFFu) - (1 << 20);
+                    o[1] = bad ? INT32_MIN : (int32_t)(((lo >> 21) | (hi << 11)) & 0x1FFFFFu) - (1 << 20);
+                    o[2] = bad ? INT32_MIN : (int32_t)(hi >> 11) - (1 << 20);
                 } else {
                     const uint16_t *v = reinterpret_cast<const uint16_t *>(raw) + 4 * src;
                     uint16_t *o = reinterpret_cast<uint16_t *>(out) + dst;

@@ -371,10 +371,9 @@ sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaSt
         }
         const long long total = t->n_seeds * (long long)t->p.inject_steps;
         if (total > 0) {
-            if (f->desc.dtype == SG_F32) streak_advect_kernel<SG_F32><<<grid_for(t, total), 256, 0, s>>>(P, f->desc.layout);
-            else if (f->desc.dtype == SG_BF16)
-                streak_advect_kernel<SG_BF16><<<grid_for(t, total), 256, 0, s>>>(P, f->desc.layout);
-            else streak_advect_kernel<SG_F16><<<grid_for(t, total), 256, 0, s>>>(P, f->desc.layout);
+            with_dtype(f->desc.dtype, [&](auto D) {
+                streak_advect_kernel<decltype(D)::value><<<grid_for(t, total), 256, 0, s>>>(P, f->desc.layout);
+            });
             SG_CUDA(cudaGetLastError());
             if (j < t->p.inject_steps) {
                 streak_release_kernel<<<grid_for(t, total), 256, 0, s>>>(P, j, 0);

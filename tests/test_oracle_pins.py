@@ -458,3 +458,28 @@ def test_golden_uniform_exit():
         F = inputs.uniform_field(g, (1.0, 0.0, 0.0))
         L = oracle.trace_streamlines(F, g.origin, g.spacing, np.array([[sx, sy, sz]]), dt=dt, max_steps=1000)
         assert L.length[0] == int(nv) and L.status[0] == int(st) and L.margin[0] == mg
+
+
+def test_fx21_codes_match_numpy_rounding_and_error_bound():
+    g = inputs.cube_grid(13)
+    F = inputs.turbulence_field(g, inputs.turbulence_modes(6, n_modes=16, kmax=3)).numpy() * np.float32(5.0)
+    F[1, 2, 3, 0] = np.inf
+    bricks = (2, 1, 2)
+    scales, codes, deq = oracle.quantize_field(F, bricks, oracle.FX21, want_codes=True)
+    n = oracle.brick_cells(g.dims, bricks)
+    for b in range(4):
+        bx, bz = b % 2, b // 2
+        ix = np.clip(bx * n[0] - 1 + np.arange(n[0] + 3), 0, 12)
+        iy = np.clip(-1 + np.arange(n[1] + 3), 0, 12)
+        iz = np.clip(bz * n[2] - 1 + np.arange(n[2] + 3), 0, 12)
+        stored = F[np.ix_(iz, iy, ix)]
+        fin = np.isfinite(stored).all(axis=-1)
+        s_b = _pow2_ceil(np.abs(stored[np.isfinite(stored)]).max())
+        assert scales[b] == np.float32(s_b / 2 ** 20)          # the quantum
+        # numpy's rint rounds half to even
+        ref = np.clip(np.rint((stored / np.float32(s_b)).astype(np.float64) * 2 ** 20), -(2 ** 20 - 1), 2 ** 20 - 1)
+        np.testing.assert_array_equal(codes[b][fin], ref[fin].astype(np.int32))
+        assert (codes[b][~fin] == np.iinfo(np.int32).min).all()
+        err = np.abs(codes[b][fin].astype(np.float64) * scales[b] - stored[fin])
+        assert err.max() <= s_b * 2.0 ** -21
+    assert np.isnan(deq[1, 2, 3]).all()
