@@ -220,6 +220,10 @@ typedef struct {
     int32_t steps_per_round; /* steps a particle may take in one round before it is
                                 re-queued in its own brick                          */
     int32_t max_rounds;    /* round cap of one trace / step call                     */
+    int32_t drain_steps;   /* once a warp finds the round's queue empty, its lanes take
+                              at most this many more steps before re-queueing their
+                              particles for the next round (0 = no limit): shortens
+                              the end of a round at the price of more rounds      */
 } sg_tracer_params;
 
 /* Fills p with the defaults (streamline, persistent kernel, eps 1e-6,
@@ -270,8 +274,12 @@ sg_status sg_tracer_check(sg_tracer *t, int32_t *rounds, void *stream);
  * advection-kernel launch, so that the kernel's own time can be read (event
  * record nodes cannot sit inside the graph's while-node).  Synchronous.
  * kernel_ms receives the summed advection-kernel time, launches the number of
- * advection-kernel launches (both nullable). */
-sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int32_t *launches, void *stream);
+ * advection-kernel launches (both nullable).  When round_ms and
+ * round_particles are given (host arrays of max_records entries), round r's
+ * kernel time and the particles its queue started with are stored for
+ * r < max_records. */
+sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int32_t *launches, float *round_ms,
+                                uint32_t *round_particles, int32_t max_records, void *stream);
 
 /* Line readback (getLines of Fig. 4), compacted to CSR: line i's vertices
  * are vertices[offsets[i] .. offsets[i+1]) (world xyz float32).  For

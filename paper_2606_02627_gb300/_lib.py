@@ -44,7 +44,7 @@ class sg_tracer_params(ctypes.Structure):
                 ("max_steps", ctypes.c_int32), ("eps", ctypes.c_float), ("tie_cells", ctypes.c_float),
                 ("tie_eps_rel", ctypes.c_float), ("inject_steps", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("steps_per_round", ctypes.c_int32),
-                ("max_rounds", ctypes.c_int32)]
+                ("max_rounds", ctypes.c_int32), ("drain_steps", ctypes.c_int32)]
 
 
 class StreamGBError(RuntimeError):
@@ -83,7 +83,7 @@ SIGNATURES = {
     "sg_tracer_step": ([P, i32, ctypes.POINTER(i32), P], i32),
     "sg_tracer_trace": ([P, P], i32),
     "sg_tracer_check": ([P, ctypes.POINTER(i32), P], i32),
-    "sg_tracer_trace_timed": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), P], i32),
+    "sg_tracer_trace_timed": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), P, P, i32, P], i32),
     "sg_tracer_get_lines": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P, P, P], i32),
     "sg_tracer_total_steps": ([P, ctypes.POINTER(i64), P], i32),
     "sg_lines_compact_static": ([P, i64, P, i64, P, P, P], i32),

@@ -150,7 +150,7 @@ class Lines:
 
 def tracer_params(dt, max_steps=1000, mode="streamline", kernel="persistent", eps=1e-6, tie_cells=1e-3,
                   tie_eps_rel=1e-3, inject_steps=1, block_size=0, blocks_per_sm=0, steps_per_round=0,
-                  max_rounds=0) -> L.sg_tracer_params:
+                  max_rounds=0, drain_steps=0) -> L.sg_tracer_params:
     p = L.sg_tracer_params()
     call("sg_tracer_params_default", ctypes.byref(p))
     p.mode = L.SG_STREAMLINE if mode == "streamline" else L.SG_STREAKLINE
@@ -165,6 +165,7 @@ def tracer_params(dt, max_steps=1000, mode="streamline", kernel="persistent", ep
     p.blocks_per_sm = int(blocks_per_sm)
     p.steps_per_round = int(steps_per_round)
     p.max_rounds = int(max_rounds)
+    p.drain_steps = int(drain_steps)
     return p
 
 
@@ -204,12 +205,19 @@ class Tracer:
     def trace(self, stream=None):
         call("sg_tracer_trace", self.h, _stream(stream))
 
-    def trace_timed(self, stream=None):
+    def trace_timed(self, stream=None, per_round=False):
         """Host-driven rounds with CUDA events around each advection kernel:
-        returns (summed kernel ms, launches)."""
+        returns (summed kernel ms, launches[, per-round ms, per-round particles])."""
         ms = ctypes.c_double()
         n = ctypes.c_int32()
-        call("sg_tracer_trace_timed", self.h, ctypes.byref(ms), ctypes.byref(n), _stream(stream))
+        cap = 4096
+        rms = np.zeros(cap, dtype=np.float32)
+        rq = np.zeros(cap, dtype=np.uint32)
+        call("sg_tracer_trace_timed", self.h, ctypes.byref(ms), ctypes.byref(n), _ptr(rms), _ptr(rq), cap,
+             _stream(stream))
+        if per_round:
+            k = min(n.value, cap)
+            return ms.value, n.value, rms[:k].copy(), rq[:k].copy()
         return ms.value, n.value
 
     def check(self, stream=None) -> int:

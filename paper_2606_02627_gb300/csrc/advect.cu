@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(256) round_kernel(const __grid_constant__ Line
     const uint32_t horizon = P.ctrl->horizon;
     bool active = false;
     bool drained = q_count == 0;
+    uint32_t drain_left = P.drain_steps;   // warp-uniform; counts down once the queue is empty
     int c[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f};
     uint32_t line = 0, step = 0, here = 0;
@@ -234,6 +235,12 @@ __global__ void __launch_bounds__(256) round_kernel(const __grid_constant__ Line
             }
         }
         if (__ballot_sync(SG_FULL_MASK, active) == 0) break;
+        // the queue is empty: give the warp's runs a few more steps, then hand
+        // them to the next round instead of holding the round open
+        if (drained) {
+            if (drain_left == 0) here = P.steps_per_round;
+            else --drain_left;
+        }
 
         int ev = EV_NONE, st = SG_LINE_ACTIVE;
         float margin = INFINITY;
@@ -523,6 +530,31 @@ static void launch_round_t(const LineParams &P, int grid, int block, int kernel,
 {
     if (kernel == SG_KERNEL_PER_STEP) per_step_kernel<DT, LAYOUT><<<grid, block, 0, s>>>(P);
     else round_kernel<DT, LAYOUT><<<grid, block, 0, s>>>(P);
+}
+
+// The advection kernels use no shared memory: ask for the whole unified
+// L1/shared array as L1, which holds the particles' current cell records.
+template <int DT, int LAYOUT>
+static cudaError_t prefer_l1_t(int kernel)
+{
+    if (kernel == SG_KERNEL_PER_STEP)
+        return cudaFuncSetAttribute(per_step_kernel<DT, LAYOUT>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    return cudaFuncSetAttribute(round_kernel<DT, LAYOUT>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+}
+
+sg_status prepare_round(sg_tracer *t)
+{
+    if (t->p.kernel == SG_KERNEL_PER_SEED) {
+        SG_CUDA(cudaFuncSetAttribute(per_seed_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        return SG_OK;
+    }
+    cudaError_t e = cudaSuccess;
+    with_dtype(t->field->desc.dtype, [&](auto D) {
+        with_layout(t->field->desc.layout,
+                    [&](auto Lay) { e = prefer_l1_t<decltype(D)::value, decltype(Lay)::value>(t->p.kernel); });
+    });
+    SG_CUDA(e);
+    return SG_OK;
 }
 
 sg_status launch_round(sg_tracer *t, cudaStream_t s)

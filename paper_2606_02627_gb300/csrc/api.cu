@@ -70,6 +70,7 @@ LineParams line_params(const sg_tracer *t)
     P.tie_eps_rel = t->p.tie_eps_rel;
     P.max_steps = (uint32_t)t->p.max_steps;
     P.steps_per_round = (uint32_t)t->p.steps_per_round;
+    P.drain_steps = (uint32_t)t->p.drain_steps;
     return P;
 }
 
@@ -151,6 +152,7 @@ static sg_status check_params(const sg_field *f, const sg_tracer_params *p)
     SG_CHECK(p->blocks_per_sm >= 0 && p->blocks_per_sm <= 32, SG_ERR_INVALID_ARG, "blocks_per_sm in [0, 32]");
     SG_CHECK(p->steps_per_round >= 0, SG_ERR_INVALID_ARG, "steps_per_round must be >= 0");
     SG_CHECK(p->max_rounds >= 0, SG_ERR_INVALID_ARG, "max_rounds must be >= 0");
+    SG_CHECK(p->drain_steps >= 0, SG_ERR_INVALID_ARG, "drain_steps must be >= 0");
     if (p->mode == SG_STREAMLINE) {
         SG_CHECK(p->max_steps >= 0 && p->max_steps < (1 << 27), SG_ERR_INVALID_ARG, "max_steps out of range");
         SG_CHECK(p->kernel == SG_KERNEL_PERSISTENT || p->kernel == SG_KERNEL_PER_SEED ||
@@ -268,9 +270,19 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
     t->nb = f->nb;
     tracer_layout(f, p, capacity, t, (char *)workspace);
     if (t->p.steps_per_round <= 0) t->p.steps_per_round = 128;
+    if (t->p.drain_steps <= 0) t->p.drain_steps = 0x7fffffff;
     t->block = p->block_size > 0 ? p->block_size : 256;
-    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : ctx->max_threads_per_sm / t->block;
+    // default: 512 resident threads per SM; more particles per SM thrash the L1
+    // that holds their cell records (measured on GB300)
+    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : (512 + t->block - 1) / t->block;
     t->grid = ctx->sm_count * (per_sm > 0 ? per_sm : 1);
+    if (t->p.mode == SG_STREAMLINE) {
+        sg_status pst = prepare_round(t);
+        if (pst) {
+            delete t;
+            return pst;
+        }
+    }
     cudaError_t e = cudaMemset(t->ctrl ? (void *)t->ctrl : (void *)t->totals, 0,
                                t->ctrl ? sizeof(Ctrl) : sizeof(int64_t) * 4);
     if (e == cudaSuccess && t->brick_count) e = cudaMemset(t->brick_count, 0, sizeof(uint32_t) * t->nb);
@@ -415,7 +427,8 @@ extern "C" sg_status sg_tracer_trace(sg_tracer *t, void *stream)
     return run_call(t, target, n, s);
 }
 
-extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int32_t *launches, void *stream)
+extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int32_t *launches, float *round_ms,
+                                           uint32_t *round_particles, int32_t max_records, void *stream)
 {
     SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
     SG_CHECK(t->p.mode == SG_STREAMLINE, SG_ERR_STATE, "trace() is for streamlines");
@@ -472,6 +485,10 @@ extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int3
             float ms = 0.f;
             if ((ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) { st = cuda_error(ce, "elapsed"); break; }
             total += ms;
+            if (round_ms && round_particles && n_launch < max_records) {
+                round_ms[n_launch] = ms;
+                round_particles[n_launch] = c.q_count;
+            }
             ++n_launch;
         }
         t->scanned = false;

@@ -25,6 +25,7 @@ struct LineParams {
     float tie_eps_rel;
     uint32_t max_steps;
     uint32_t steps_per_round;
+    uint32_t drain_steps;        // steps left to a warp's lanes once the round's queue is empty
     double origin_d[3];
     double spacing_d[3];
 };
@@ -86,6 +87,7 @@ sg_status launch_per_seed(sg_tracer *t, cudaStream_t s);
 sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStream_t s, bool in_graph,
                      unsigned long long cond_handle, int mode);
 sg_status launch_round(sg_tracer *t, cudaStream_t s);
+sg_status prepare_round(sg_tracer *t);
 sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s);
 sg_status launch_iota(int32_t *dst, int64_t n, cudaStream_t s);
 sg_status streak_upload(sg_tracer *t, cudaStream_t s);
