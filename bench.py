@@ -63,6 +63,11 @@ def parse():
     ap.add_argument("--per-step", action="store_true", help="also time the one-launch-per-step kernel")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--schedule", default="", help="block,blocks_per_sm,steps_per_round")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the rounds from the host (sg_tracer_trace_timed) instead of the CUDA graph, so that "
+                         "a profiler sees every advection-kernel launch")
+    ap.add_argument("--once", action="store_true",
+                    help="profiling case: one step of the headline form, then print its particle-steps and exit")
     return ap.parse_args()
 
 
@@ -269,7 +274,10 @@ def main():
     def one_step(fld, tr, out_off, out_vert, out_st, seeds):
         fld.set_global(F, stream=stream)                     # a1: bricks, ghosts, encode
         tr.upload_seeds(seeds, stream=stream)               # a2: seeds -> per-brick queues
-        tr.trace(stream=stream)                             # a3-a7: rounds of the persistent kernel
+        if args.host_loop:
+            tr.trace_timed(stream=stream)                   # a3-a7, rounds driven from the host
+        else:
+            tr.trace(stream=stream)                         # a3-a7: rounds of the persistent kernel (graph)
         L = api.L
         api.call("sg_tracer_get_lines", tr.h, None, None, api._ptr(out_off), api._ptr(out_vert),
                  api._ptr(out_st), None, None, api._stream(stream))    # a8: CSR
@@ -321,6 +329,13 @@ def main():
 
     # headline: the chosen storage type, persistent form
     fld, tr = make(args.dtype, args.layout, "persistent")
+    if args.once:
+        one_step(fld, tr, None, None, None, seeds_dev)
+        stream.synchronize()
+        print(json.dumps({"once": True, "particle_steps": tr.total_steps(stream=stream),
+                          "rounds": tr.check(stream=stream), "dtype": args.dtype, "layout": args.layout,
+                          "n": n, "seeds": args.seeds, "max_steps": args.max_steps}))
+        return
     with Clocks(uuid) as clk:
         ms, tot, tot_all, _ = timed(fld, tr, args.warmup, args.steps, seeds_dev)
     clocks = clk.summary()

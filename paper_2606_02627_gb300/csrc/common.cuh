@@ -274,7 +274,32 @@ template <int DT>
 __device__ __forceinline__ float3 trilerp_record(const typename Elem<DT>::T *__restrict__ rec, float fx, float fy,
                                                  float fz)
 {
-    if constexpr (DT == SG_F32) {
+    if constexpr (DT == SG_FX21) {
+        // x pairs interpolate the biased floats 2^23 + u directly: their
+        // difference is exact, and the bias leaves with the lower corner
+        // (the same value as subtracting it from both corners first)
+        const uint4 *r = reinterpret_cast<const uint4 *>(rec);
+        const uint4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
+        const float C = 9437184.0f;
+        auto raw = [](unsigned lo, unsigned hi) {
+            return make_float3(__int_as_float(0x4B000000u | (lo & FX21_MASK)),
+                               __int_as_float(0x4B000000u | (__funnelshift_r(lo, hi, 21) & FX21_MASK)),
+                               __int_as_float(0x4B000000u | (hi >> 11)));
+        };
+        auto xl = [&](float3 p, float3 q) {
+            return make_float3(fmaf(fx, q.x - p.x, p.x - C), fmaf(fx, q.y - p.y, p.y - C), fmaf(fx, q.z - p.z, p.z - C));
+        };
+        const float3 x00 = xl(raw(a.x, a.y), raw(a.z, a.w));   // (y0, z0)
+        const float3 x10 = xl(raw(b.x, b.y), raw(b.z, b.w));   // (y1, z0)
+        const float3 x01 = xl(raw(c.x, c.y), raw(c.z, c.w));   // (y0, z1)
+        const float3 x11 = xl(raw(d.x, d.y), raw(d.z, d.w));   // (y1, z1)
+        float3 v;
+        v.x = lerpf(lerpf(x00.x, x10.x, fy), lerpf(x01.x, x11.x, fy), fz);
+        v.y = lerpf(lerpf(x00.y, x10.y, fy), lerpf(x01.y, x11.y, fy), fz);
+        v.z = lerpf(lerpf(x00.z, x10.z, fy), lerpf(x01.z, x11.z, fy), fz);
+        if ((a.y | a.w | b.y | b.w | c.y | c.w | d.y | d.w) & FX21_FLAG) v = make_float3(NAN, NAN, NAN);
+        return v;
+    } else if constexpr (DT == SG_F32) {
         const float4 *r = reinterpret_cast<const float4 *>(rec);
         const float4 a0 = __ldg(r), a1 = __ldg(r + 1), a2 = __ldg(r + 2), a3 = __ldg(r + 3);
         const float4 a4 = __ldg(r + 4), a5 = __ldg(r + 5), a6 = __ldg(r + 6), a7 = __ldg(r + 7);
@@ -283,14 +308,10 @@ __device__ __forceinline__ float3 trilerp_record(const typename Elem<DT>::T *__r
     } else {
         const uint4 *r = reinterpret_cast<const uint4 *>(rec);
         const uint4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
-        float3 v = lerp8(decode_elem<DT>(make_uint2(a.x, a.y)), decode_elem<DT>(make_uint2(a.z, a.w)),
-                         decode_elem<DT>(make_uint2(b.x, b.y)), decode_elem<DT>(make_uint2(b.z, b.w)),
-                         decode_elem<DT>(make_uint2(c.x, c.y)), decode_elem<DT>(make_uint2(c.z, c.w)),
-                         decode_elem<DT>(make_uint2(d.x, d.y)), decode_elem<DT>(make_uint2(d.z, d.w)), fx, fy, fz);
-        if constexpr (DT == SG_FX21) {
-            if ((a.y | a.w | b.y | b.w | c.y | c.w | d.y | d.w) & FX21_FLAG) v = make_float3(NAN, NAN, NAN);
-        }
-        return v;
+        return lerp8(decode_elem<DT>(make_uint2(a.x, a.y)), decode_elem<DT>(make_uint2(a.z, a.w)),
+                     decode_elem<DT>(make_uint2(b.x, b.y)), decode_elem<DT>(make_uint2(b.z, b.w)),
+                     decode_elem<DT>(make_uint2(c.x, c.y)), decode_elem<DT>(make_uint2(c.z, c.w)),
+                     decode_elem<DT>(make_uint2(d.x, d.y)), decode_elem<DT>(make_uint2(d.z, d.w)), fx, fy, fz);
     }
 }
 

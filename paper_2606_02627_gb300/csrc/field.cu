@@ -92,15 +92,14 @@ __global__ void brick_scale_kernel(unsigned *maxbits, float *scales, int b0, int
     maxbits[b0 + i] = 0u;   // ready for the next store
 }
 
+// Encoding of one sample (x, y, z) with the brick's scale (FP32: as given).
 template <int DT>
-__device__ __forceinline__ void store_elem(char *brick, long long idx, float x, float y, float z, float inv_scale_unused,
-                                           float scale);
+__device__ __forceinline__ typename Elem<DT>::T encode_elem(float x, float y, float z, float scale);
 
 template <>
-__device__ __forceinline__ void store_elem<SG_F32>(char *brick, long long idx, float x, float y, float z, float,
-                                                   float)
+__device__ __forceinline__ float4 encode_elem<SG_F32>(float x, float y, float z, float)
 {
-    reinterpret_cast<float4 *>(brick)[idx] = make_float4(x, y, z, 0.0f);
+    return make_float4(x, y, z, 0.0f);
 }
 
 // code = round-to-nearest-even(v / s) in the storage format; the quotient is an
@@ -108,23 +107,21 @@ __device__ __forceinline__ void store_elem<SG_F32>(char *brick, long long idx, f
 __device__ __forceinline__ float scaled(float v, float s) { return (fabsf(v) < INFINITY) ? v / s : __int_as_float(0x7fc00000); }
 
 template <>
-__device__ __forceinline__ void store_elem<SG_BF16>(char *brick, long long idx, float x, float y, float z, float,
-                                                    float s)
+__device__ __forceinline__ uint2 encode_elem<SG_BF16>(float x, float y, float z, float s)
 {
     const unsigned short bx = __bfloat16_as_ushort(__float2bfloat16_rn(scaled(x, s)));
     const unsigned short by = __bfloat16_as_ushort(__float2bfloat16_rn(scaled(y, s)));
     const unsigned short bz = __bfloat16_as_ushort(__float2bfloat16_rn(scaled(z, s)));
-    reinterpret_cast<uint2 *>(brick)[idx] = make_uint2((unsigned)bx | ((unsigned)by << 16), (unsigned)bz);
+    return make_uint2((unsigned)bx | ((unsigned)by << 16), (unsigned)bz);
 }
 
 template <>
-__device__ __forceinline__ void store_elem<SG_F16>(char *brick, long long idx, float x, float y, float z, float,
-                                                   float s)
+__device__ __forceinline__ uint2 encode_elem<SG_F16>(float x, float y, float z, float s)
 {
     const unsigned short hx = __half_as_ushort(__float2half_rn(scaled(x, s)));
     const unsigned short hy = __half_as_ushort(__float2half_rn(scaled(y, s)));
     const unsigned short hz = __half_as_ushort(__float2half_rn(scaled(z, s)));
-    reinterpret_cast<uint2 *>(brick)[idx] = make_uint2((unsigned)hx | ((unsigned)hy << 16), (unsigned)hz);
+    return make_uint2((unsigned)hx | ((unsigned)hy << 16), (unsigned)hz);
 }
 
 // FX21: q = round-to-nearest-even(v / quantum), clamped to +-(2^20 - 1), stored
@@ -142,48 +139,79 @@ __device__ __forceinline__ unsigned fx21_code(float v, float quantum, unsigned &
 }
 
 template <>
-__device__ __forceinline__ void store_elem<SG_FX21>(char *brick, long long idx, float x, float y, float z, float,
-                                                    float quantum)
+__device__ __forceinline__ uint2 encode_elem<SG_FX21>(float x, float y, float z, float quantum)
 {
     unsigned flag = 0;
     const unsigned ux = fx21_code(x, quantum, flag);
     const unsigned uy = fx21_code(y, quantum, flag);
     const unsigned uz = fx21_code(z, quantum, flag);
-    const unsigned lo = ux | (uy << 21);
-    const unsigned hi = (uy >> 11) | flag | (uz << 11);
-    reinterpret_cast<uint2 *>(brick)[idx] = make_uint2(lo, hi);
+    return make_uint2(ux | (uy << 21), (uy >> 11) | flag | (uz << 11));
 }
 
+// Source sample of stored coordinate (sx, sy, sz) of brick (bx, by, bz).
+__device__ __forceinline__ const float *src_at(const StoreArgs &A, int bx, int by, int bz, int sx, int sy, int sz)
+{
+    const DevField &F = A.F;
+    if (A.src_mode == 1) return A.src + 3 * (((long long)sz * F.S[1] + sy) * F.S[0] + sx);
+    const int gx = clampi(bx * F.n[0] - 1 + sx, 0, F.nm1[0]);
+    const int gy = clampi(by * F.n[1] - 1 + sy, 0, F.nm1[1]);
+    const int gz = clampi(bz * F.n[2] - 1 + sz, 0, F.nm1[2]);
+    return A.src + 3 * (((long long)gz * F.dims[1] + gy) * F.dims[0] + gx);
+}
+
+// Sample layouts (LINEAR, TILED4): one thread per stored sample.
 template <int DT>
 __global__ void brick_store_kernel(StoreArgs A, int layout)
 {
+    using T = typename Elem<DT>::T;
     const DevField &F = A.F;
     const int b = A.brick0 + blockIdx.y;
-    char *brick = A.data + (long long)b * A.brick_bytes;
+    const int bx = b % F.B[0], by = (b / F.B[0]) % F.B[1], bz = b / (F.B[0] * F.B[1]);
+    T *brick = reinterpret_cast<T *>(A.data + (long long)b * A.brick_bytes);
     const float s = (DT == SG_F32) ? 1.0f : A.scales[b];
-    if (layout == SG_LAYOUT_CELL8) {
-        // one thread per stored element: cell record r >> 3, corner r & 7
-        const long long total = F.brick_elems;
-        for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total;
-             r += (long long)gridDim.x * blockDim.x) {
-            const long long cell = r >> 3;
-            const int corner = (int)(r & 7);
-            const int cx = (int)(cell % F.C[0]);
-            const int cy = (int)((cell / F.C[0]) % F.C[1]);
-            const int cz = (int)(cell / ((long long)F.C[0] * F.C[1]));
-            const float *src = src_sample(A, b, cx + (corner & 1), cy + ((corner >> 1) & 1), cz + (corner >> 2));
-            store_elem<DT>(brick, r, src[0], src[1], src[2], 0.0f, s);
-        }
-        return;
+    const int total = F.S[0] * F.S[1] * F.S[2];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
+        const int sx = r % F.S[0];
+        const int t = r / F.S[0];
+        const int sy = t % F.S[1];
+        const int sz = t / F.S[1];
+        const float *src = src_at(A, bx, by, bz, sx, sy, sz);
+        brick[storage_index(layout, sx, sy, sz, F)] = encode_elem<DT>(src[0], src[1], src[2], s);
     }
-    const long long total = (long long)F.S[0] * F.S[1] * F.S[2];
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total;
-         r += (long long)gridDim.x * blockDim.x) {
-        const int sx = (int)(r % F.S[0]);
-        const int sy = (int)((r / F.S[0]) % F.S[1]);
-        const int sz = (int)(r / ((long long)F.S[0] * F.S[1]));
-        const float *src = src_sample(A, b, sx, sy, sz);
-        store_elem<DT>(brick, storage_index(layout, sx, sy, sz, F), src[0], src[1], src[2], 0.0f, s);
+}
+
+// CELL8: one thread per cell record; the eight corners are encoded in
+// registers and written as one contiguous 64- or 128-byte record.
+template <int DT>
+__global__ void brick_store_cell8_kernel(StoreArgs A)
+{
+    using T = typename Elem<DT>::T;
+    const DevField &F = A.F;
+    const int b = A.brick0 + blockIdx.y;
+    const int bx = b % F.B[0], by = (b / F.B[0]) % F.B[1], bz = b / (F.B[0] * F.B[1]);
+    T *brick = reinterpret_cast<T *>(A.data + (long long)b * A.brick_bytes);
+    const float s = (DT == SG_F32) ? 1.0f : A.scales[b];
+    const int cells = F.C[0] * F.C[1] * F.C[2];
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < cells; cell += gridDim.x * blockDim.x) {
+        const int cx = cell % F.C[0];
+        const int t = cell / F.C[0];
+        const int cy = t % F.C[1];
+        const int cz = t / F.C[1];
+        T e[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float *src = src_at(A, bx, by, bz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
+            e[k] = encode_elem<DT>(src[0], src[1], src[2], s);
+        }
+        T *rec = brick + (long long)cell * 8;
+        if constexpr (DT == SG_F32) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) reinterpret_cast<float4 *>(rec)[k] = e[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                reinterpret_cast<uint4 *>(rec)[k] = make_uint4(e[2 * k].x, e[2 * k].y, e[2 * k + 1].x, e[2 * k + 1].y);
+        }
     }
 }
 
@@ -262,7 +290,8 @@ sg_status launch_brick_store(sg_field *f, int slot, const float *src, int src_mo
     const int b0 = src_mode == 1 ? brick_index : 0;
     const int nbr = src_mode == 1 ? 1 : f->nb;
     A.brick0 = b0;
-    const long long total = d.layout == SG_LAYOUT_CELL8 ? A.F.brick_elems : (long long)A.F.S[0] * A.F.S[1] * A.F.S[2];
+    const long long total = d.layout == SG_LAYOUT_CELL8 ? (long long)A.F.C[0] * A.F.C[1] * A.F.C[2]
+                                                        : (long long)A.F.S[0] * A.F.S[1] * A.F.S[2];
     const int block = 256;
     dim3 grid(grid_x_for(total, block, nbr, f->ctx->sm_count), nbr);
     if (d.dtype != SG_F32) {
@@ -273,7 +302,10 @@ sg_status launch_brick_store(sg_field *f, int slot, const float *src, int src_mo
     brick_scale_kernel<<<(nbr + 255) / 256, 256, 0, s>>>(f->maxbits, A.scales, b0, nbr,
                                                          d.dtype == SG_FX21 ? 1.0f / 1048576.0f : 1.0f);
     SG_CUDA(cudaGetLastError());
-    const bool ok = with_dtype(d.dtype, [&](auto D) { brick_store_kernel<decltype(D)::value><<<grid, block, 0, s>>>(A, d.layout); });
+    const bool ok = with_dtype(d.dtype, [&](auto D) {
+        if (d.layout == SG_LAYOUT_CELL8) brick_store_cell8_kernel<decltype(D)::value><<<grid, block, 0, s>>>(A);
+        else brick_store_kernel<decltype(D)::value><<<grid, block, 0, s>>>(A, d.layout);
+    });
     SG_CHECK(ok, SG_ERR_UNSUPPORTED, "unsupported dtype %d", d.dtype);
     SG_CUDA(cudaGetLastError());
     return SG_OK;

@@ -157,7 +157,7 @@ def test_bricked_equals_single_brick_bit_exact(ctx, dtype, layout):
             # scale: a ghost copy may decode differently from its owner when the
             # two bricks' scales differ
             d = ((o.vertices - out[0].vertices).abs() / torch.tensor(g.spacing, device=o.vertices.device)).max()
-            assert d.item() < 1e-3
+            assert d.item() < (1e-3 if dtype == "f16" else 5e-2)
         else:
             assert torch.equal(o.vertices, out[0].vertices)
 
