@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--per-step", action="store_true", help="also time the one-launch-per-step kernel")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--schedule", default="", help="block,blocks_per_sm,steps_per_round")
+    ap.add_argument("--config", default="steady", choices=["steady", "streak"],
+                    help="steady: brick-decomposed streamlines (the headline); streak: unsteady streaklines with "
+                         "time slices streamed from page-locked host memory")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the rounds from the host (sg_tracer_trace_timed) instead of the CUDA graph, so that "
                          "a profiler sees every advection-kernel launch")
@@ -183,9 +186,87 @@ def cpu_oracle_rate(F_host, grid, seeds, dt, max_steps, seconds):
     return steps / t0, nthreads, n, steps, t0
 
 
+def run_streak(args, rank, world, local):
+    """Unsteady streaklines: 64 time slices of a 256^3 FP32 field (phases advancing in time, seed 3) in
+    page-locked host memory, streamed one slice per step into three resident slots on a side stream;
+    4096 release points (64 rakes x 64 points) each release one particle per step for 64 steps."""
+    import numpy as np
+    import torch
+    from paper_2606_02627_gb300 import api, inputs
+    from paper_2606_02627_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    n, n_slices, rakes, per_rake = 256, 64, 64, 64
+    g = inputs.cube_grid(n)
+    modes = inputs.turbulence_modes(3)
+    ctx = api.Context(local)
+    host = torch.empty((n_slices, n, n, n, 3), dtype=torch.float32).pin_memory()
+    vref = 0.0
+    for s in range(n_slices):
+        F = inputs.turbulence_field(g, modes, time_slice=s, n_slices=n_slices, device=dev)
+        sp = torch.tensor(g.spacing, device=dev, dtype=torch.float32)
+        vref = max(vref, float((F / sp).norm(dim=-1).max()))
+        host[s].copy_(F)
+        del F
+    dt = args.h / vref
+    # rakes: segments between two uniform points in the interior, 64 release points each
+    u = inputs.uniform(3 + 1000 * rank, 9, rakes * 6).reshape(rakes, 6)
+    a = 8 + (n - 17) * u[:, :3]
+    b = 8 + (n - 17) * u[:, 3:]
+    rel = np.concatenate([inputs.rake_seeds(g, per_rake, a[r], b[r]) for r in range(rakes)])
+    rel_dev = torch.from_numpy(rel).to(dev)
+    fld = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(2, 2, 2), dtype="f32", layout="linear", n_slots=3,
+                    slice_dt=dt)
+    tr = api.Tracer(ctx, fld, capacity=len(rel), dt=dt, mode="streakline", inject_steps=per_rake)
+    main_s = torch.cuda.Stream(device=dev)
+    side = torch.cuda.Stream(device=dev)
+
+    def run_once():
+        fld.stream_slice(0, host[0], stream=side)
+        fld.stream_slice(1, host[1], stream=side)
+        tr.upload_seeds(rel_dev, stream=main_s)
+        for j in range(1, n_slices):
+            if j + 1 < n_slices:
+                fld.stream_slice(j + 1, host[j + 1], stream=side)
+            tr.step(1, sync=False, stream=main_s)
+        tr.sizes(stream=main_s)                 # CSR scan of the streaklines
+
+    run_once()
+    torch.cuda.synchronize(dev)
+    steps = tr.total_steps(stream=main_s)
+    for _ in range(args.warmup):
+        run_once()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(side)
+    for _ in range(args.steps):
+        run_once()
+    main_s.wait_stream(side)
+    e1.record(main_s)
+    e1.synchronize()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    nl, nv = tr.sizes(stream=main_s)
+    h2d = n_slices * n ** 3 * 12
+    out = {"metric": "RK4 particle-steps/s (streaklines)", "value": steps / (ms / 1e3), "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"streaklines: {n_slices} slices of {n}^3 FP32 turbulence (seed 3) streamed from "
+                                  f"page-locked host memory, {rakes * per_rake} release points x {per_rake} releases, "
+                                  f"RK4 h={args.h} cell", "slots": 3, "bricks": "2x2x2"},
+           "particle_steps_per_step": steps, "h2d_bytes_per_step": h2d, "h2d_gbs": h2d / (ms / 1e3) / 1e9,
+           "streaklines": nl, "vertices": nv}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.config == "streak":
+        return run_streak(args, rank, world, local)
     import numpy as np
     import torch
 

@@ -192,19 +192,23 @@ __global__ void streak_release_kernel(const __grid_constant__ StreakParams P, in
 
 // Per release point: live particles (low 40 bits) and runs of consecutive live
 // particles (high 24 bits), packed for one scan.
-__global__ void streak_count_kernel(const uint8_t *status, long long R, int inj, int births,
-                                    unsigned long long *packed)
+// Also adds every released particle's successful steps to *steps_total.
+__global__ void streak_count_kernel(const uint8_t *status, const Particle *state, long long R, int inj, int births,
+                                    unsigned long long *packed, unsigned long long *steps_total)
 {
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (long long)gridDim.x * blockDim.x) {
-        unsigned long long live = 0, runs = 0;
+        unsigned long long live = 0, runs = 0, steps = 0;
         bool prev = false;
         for (int b = 0; b < births; ++b) {
-            const bool l = status[r * inj + b] == SG_LINE_ACTIVE;
+            const uint8_t st = status[r * inj + b];
+            const bool l = st == SG_LINE_ACTIVE;
             live += l;
             runs += (l && !prev);
             prev = l;
+            if (st != 255 && st != SG_LINE_OUT) steps += state[r * inj + b].step;
         }
         packed[r] = live + (runs << 40);
+        atomicAdd(steps_total, steps);
     }
 }
 
@@ -246,7 +250,6 @@ __global__ void scan_u64_kernel(const unsigned long long *in, long long n, unsig
         excl[n] = carry;
         totals[0] = (int64_t)(carry & ((1ull << 40) - 1));   // vertices
         totals[1] = (int64_t)(carry >> 40);                  // lines
-        totals[2] = 0;
     }
 }
 
@@ -399,8 +402,10 @@ sg_status launch_streak_scan(sg_tracer *t, cudaStream_t s)
     const long long R = t->n_seeds;
     unsigned long long *packed = t->block_sums;      // R + 2 entries are carved for this
     unsigned long long *excl = reinterpret_cast<unsigned long long *>(t->offsets);
+    SG_CUDA(cudaMemsetAsync(t->totals + 2, 0, sizeof(int64_t), s));
     if (R > 0) {
-        streak_count_kernel<<<grid_for(t, R), 256, 0, s>>>(t->sk_status, R, t->p.inject_steps, t->births, packed);
+        streak_count_kernel<<<grid_for(t, R), 256, 0, s>>>(t->sk_status, t->sk_state, R, t->p.inject_steps, t->births,
+                                                           packed, reinterpret_cast<unsigned long long *>(t->totals + 2));
         SG_CUDA(cudaGetLastError());
     }
     scan_u64_kernel<<<1, 1024, 0, s>>>(packed, R, excl, t->totals);
