@@ -300,6 +300,72 @@ sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t *n_vertice
  * the particle-steps/s metric).  Synchronous. */
 sg_status sg_tracer_total_steps(sg_tracer *t, int64_t *steps, void *stream);
 
+/* -------------------------------------------------------------- request batch */
+
+/* Continuous batching of streamline requests over resident fields: the
+ * serving form of the paper's interactive seed-placement application
+ * (Sec. 4), where seed regions arrive while earlier ones are being traced.
+ * Requests (seeds + tracer parameters + one resident field) are admitted
+ * while line slots and slab memory are free, and their particles share the
+ * per-brick queues and the persistent kernel of one CUDA-graph launch per
+ * sg_batch_run; a request's lines are read back as soon as its last line
+ * stops, and its memory then serves later requests.  Every particle's
+ * arithmetic is the same as in a tracer: a request's lines are identical
+ * whether it runs alone or among others.
+ *
+ * All fields of a batch must share one layout (desc.layout); their storage
+ * types may differ (each lane decodes its own request's type). */
+typedef struct {
+    int64_t max_lines;       /* line slots: lines of admitted, not yet released requests */
+    int64_t slab_bytes;      /* vertex slab pool ((max_steps+1) * 12 B per line of a request) */
+    int32_t max_requests;    /* request table entries (<= 1048576) */
+    int32_t max_fields;      /* distinct fields used by requests (<= 64) */
+    int32_t max_bricks;      /* bricks summed over those fields (<= 65536) */
+    int32_t layout;          /* field layout of every request's field */
+    int32_t block_size;      /* schedule of the persistent kernel (0 = default) */
+    int32_t blocks_per_sm;
+    int32_t steps_per_round;
+} sg_batch_desc;
+
+/* Device bytes of a batch (slab pool, line arrays, queues, request table,
+ * scan scratch). */
+sg_status sg_batch_required_bytes(const sg_context *ctx, const sg_batch_desc *desc, size_t *bytes);
+sg_status sg_batch_create(sg_context *ctx, const sg_batch_desc *desc, void *workspace, size_t bytes,
+                          sg_batch **out);
+sg_status sg_batch_destroy(sg_batch *b);
+
+/* Free line slots and the largest free slab extent (bytes), for admission. */
+sg_status sg_batch_capacity(const sg_batch *b, int64_t *free_lines, int64_t *largest_slab_bytes,
+                            int32_t *free_requests);
+
+/* Admits a request: n seeds (world xyz float32, host or device memory) traced
+ * on field f with p (dt, max_steps, eps, tie thresholds; mode must be
+ * SG_STREAMLINE; the schedule fields are ignored).  Returns SG_ERR_OOM,
+ * leaving the batch unchanged, when the request does not fit now (line
+ * slots, slab pool, request table or brick keys); the caller keeps it queued
+ * and retries after releasing finished requests.  The seeds are copied and
+ * binned on `stream`; they join the next sg_batch_run. */
+sg_status sg_batch_submit(sg_batch *b, sg_field *f, const float *xyz, int64_t n, const sg_tracer_params *p,
+                          int64_t *request_id, void *stream);
+
+/* Runs up to max_rounds rounds of the persistent kernel over all admitted
+ * requests (one CUDA-graph launch; max_rounds <= 0 runs until every queue is
+ * empty).  Asynchronous. */
+sg_status sg_batch_run(sg_batch *b, int32_t max_rounds, void *stream);
+
+/* Synchronises `stream` and lists requests whose lines have all stopped and
+ * that were not listed before: up to cap ids into ids (host), *count set. */
+sg_status sg_batch_finished(sg_batch *b, int64_t *ids, int32_t cap, int32_t *count, void *stream);
+
+/* Lines of a request, as sg_tracer_get_lines (two calls: sizes with NULL
+ * buffers, then the buffers; device or page-locked host). */
+sg_status sg_batch_get_lines(sg_batch *b, int64_t request_id, int64_t *n_lines, int64_t *n_vertices,
+                             int64_t *offsets, float *vertices, uint8_t *status, float *margin, void *stream);
+
+/* Frees a request's line slots and slab once the work queued on `stream`
+ * (its readback) is done.  Its id becomes invalid. */
+sg_status sg_batch_release(sg_batch *b, int64_t request_id, void *stream);
+
 /* ------------------------------------------------ allocation-free compaction */
 
 /* The paper has no counterpart to this call: it is a service for callers that

@@ -47,6 +47,13 @@ class sg_tracer_params(ctypes.Structure):
                 ("max_rounds", ctypes.c_int32), ("drain_steps", ctypes.c_int32)]
 
 
+class sg_batch_desc(ctypes.Structure):
+    _fields_ = [("max_lines", ctypes.c_int64), ("slab_bytes", ctypes.c_int64), ("max_requests", ctypes.c_int32),
+                ("max_fields", ctypes.c_int32), ("max_bricks", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("steps_per_round", ctypes.c_int32)]
+
+
 class StreamGBError(RuntimeError):
     def __init__(self, fn, code, msg):
         super().__init__(f"{fn} -> {ERR_NAMES.get(code, code)}: {msg}")
@@ -87,6 +94,15 @@ SIGNATURES = {
     "sg_tracer_get_lines": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P, P, P], i32),
     "sg_tracer_total_steps": ([P, ctypes.POINTER(i64), P], i32),
     "sg_lines_compact_static": ([P, i64, P, i64, P, P, P], i32),
+    "sg_batch_required_bytes": ([P, ctypes.POINTER(sg_batch_desc), ctypes.POINTER(sz)], i32),
+    "sg_batch_create": ([P, ctypes.POINTER(sg_batch_desc), P, sz, PP], i32),
+    "sg_batch_destroy": ([P], i32),
+    "sg_batch_capacity": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)], i32),
+    "sg_batch_submit": ([P, P, P, i64, ctypes.POINTER(sg_tracer_params), ctypes.POINTER(i64), P], i32),
+    "sg_batch_run": ([P, i32, P], i32),
+    "sg_batch_finished": ([P, P, i32, ctypes.POINTER(i32), P], i32),
+    "sg_batch_get_lines": ([P, i64, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P, P], i32),
+    "sg_batch_release": ([P, i64, P], i32),
 }
 
 _lock = threading.Lock()

@@ -263,3 +263,93 @@ class Tracer:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Continuous batching of streamline requests (sg_batch_*): requests join
+    between runs and leave when their last line stops."""
+
+    def __init__(self, ctx: Context, max_lines: int, slab_bytes: int, layout="cell8", max_requests=1024,
+                 max_fields=16, max_bricks=4096, block_size=0, blocks_per_sm=0, steps_per_round=0):
+        self.ctx = ctx
+        d = L.sg_batch_desc()
+        d.max_lines = int(max_lines)
+        d.slab_bytes = int(slab_bytes)
+        d.max_requests = int(max_requests)
+        d.max_fields = int(max_fields)
+        d.max_bricks = int(max_bricks)
+        d.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+        d.block_size = int(block_size)
+        d.blocks_per_sm = int(blocks_per_sm)
+        d.steps_per_round = int(steps_per_round)
+        self.desc = d
+        nbytes = ctypes.c_size_t()
+        call("sg_batch_required_bytes", ctx.h, ctypes.byref(d), ctypes.byref(nbytes))
+        self.nbytes = nbytes.value
+        self.workspace = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=f"cuda:{ctx.device}")
+        h = ctypes.c_void_p()
+        call("sg_batch_create", ctx.h, ctypes.byref(d), _ptr(self.workspace), self.nbytes, ctypes.byref(h))
+        self.h = h
+        self._keep = {}
+
+    def capacity(self):
+        fl = ctypes.c_int64()
+        sb = ctypes.c_int64()
+        fr = ctypes.c_int32()
+        call("sg_batch_capacity", self.h, ctypes.byref(fl), ctypes.byref(sb), ctypes.byref(fr))
+        return fl.value, sb.value, fr.value
+
+    def submit(self, field: Field, xyz, dt, max_steps, eps=1e-6, tie_cells=1e-3, tie_eps_rel=1e-3, stream=None):
+        """Returns the request id, or None when the request does not fit now."""
+        if isinstance(xyz, np.ndarray):
+            xyz = torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.float32))
+        xyz = xyz.contiguous()
+        p = tracer_params(dt=dt, max_steps=max_steps, eps=eps, tie_cells=tie_cells, tie_eps_rel=tie_eps_rel)
+        rid = ctypes.c_int64()
+        code = L.lib().sg_batch_submit(self.h, field.h, _ptr(xyz), int(xyz.shape[0]), ctypes.byref(p),
+                                       ctypes.byref(rid), _stream(stream))
+        if code == L.SG_ERR_OOM:
+            return None
+        L.check("sg_batch_submit", code)
+        self._keep[rid.value] = xyz
+        return rid.value
+
+    def run(self, max_rounds: int = 0, stream=None):
+        call("sg_batch_run", self.h, int(max_rounds), _stream(stream))
+
+    def finished(self, stream=None):
+        cap = 4096
+        ids = np.zeros(cap, dtype=np.int64)
+        n = ctypes.c_int32()
+        call("sg_batch_finished", self.h, _ptr(ids), cap, ctypes.byref(n), _stream(stream))
+        return [int(x) for x in ids[: n.value]]
+
+    def get_lines(self, rid: int, device="cuda", stream=None) -> Lines:
+        nl = ctypes.c_int64()
+        nv = ctypes.c_int64()
+        call("sg_batch_get_lines", self.h, rid, ctypes.byref(nl), ctypes.byref(nv), None, None, None, None,
+             _stream(stream))
+        kw = dict(pin_memory=True) if device == "pinned" else dict(device=f"cuda:{self.ctx.device}")
+        off = torch.empty(nl.value + 1, dtype=torch.int64, **kw)
+        vert = torch.empty((max(nv.value, 1), 3), dtype=torch.float32, **kw)
+        st = torch.empty(max(nl.value, 1), dtype=torch.uint8, **kw)
+        mg = torch.empty(max(nl.value, 1), dtype=torch.float32, **kw)
+        call("sg_batch_get_lines", self.h, rid, None, None, _ptr(off), _ptr(vert), _ptr(st), _ptr(mg),
+             _stream(stream))
+        src = torch.zeros(max(nl.value, 1), dtype=torch.int32)
+        return Lines(off, vert[: nv.value], st[: nl.value], mg[: nl.value], src[: nl.value])
+
+    def release(self, rid: int, stream=None):
+        call("sg_batch_release", self.h, rid, _stream(stream))
+        self._keep.pop(rid, None)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib().sg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -167,6 +167,33 @@ sg_status launch_gather_lines(sg_tracer *t, int64_t *offsets, float *vertices, u
     return SG_OK;
 }
 
+// Scan + gather for a contiguous range of lines whose slabs start at `slab`
+// (the request lines of a batch).  scan_only: offsets and totals only.
+sg_status launch_compact_range(const uint32_t *len, long long n, const float *slab, long long W, const uint8_t *st_in,
+                               const float *mg_in, unsigned long long *block_sums, int64_t *dev_offsets,
+                               int64_t *totals, int64_t *offsets_out, float *vertices, uint8_t *status_out,
+                               float *margin_out, int sm_count, bool scan_only, cudaStream_t s)
+{
+    const long long nblocks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (scan_only) {
+        if (nblocks > 0) {
+            scan_reduce_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(len, n, block_sums);
+            SG_CUDA(cudaGetLastError());
+        }
+        scan_blocks_kernel<<<1, SCAN_THREADS, 0, s>>>(block_sums, nblocks, totals, dev_offsets, n);
+        SG_CUDA(cudaGetLastError());
+        if (nblocks > 0) {
+            scan_apply_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(len, n, block_sums, dev_offsets);
+            SG_CUDA(cudaGetLastError());
+        }
+        return SG_OK;
+    }
+    gather_lines_kernel<<<sm_count * 8, 256, 0, s>>>(slab, W, len, dev_offsets, n, vertices, st_in, status_out, mg_in,
+                                                     margin_out, offsets_out);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
 // ------------------------------------------------------------------ allocation-free compaction
 //
 // Scratch of sg_lines_compact_static: one 64-bit sum per chunk of SCAN_CHUNK

@@ -12,20 +12,15 @@
 
 namespace sg {
 
-struct BinArgs {
-    const Particle *src;
-    uint32_t *src_count;
-    Particle *dst;
-    uint32_t *brick_count;
-    uint32_t *brick_cursor;
-    Ctrl *ctrl;
-    int n[3];
-    int B[3];
-    int nb;
-};
-
-__device__ __forceinline__ int brick_id(const BinArgs &A, int cx, int cy, int cz)
+__device__ __forceinline__ int brick_key(const BinArgs &A, uint32_t line, int cx, int cy, int cz)
 {
+    if (A.line_req) {
+        const ReqDev &R = A.reqs[A.line_req[line]];
+        const int bx = min(cx / R.F.n[0], R.F.B[0] - 1);
+        const int by = min(cy / R.F.n[1], R.F.B[1] - 1);
+        const int bz = min(cz / R.F.n[2], R.F.B[2] - 1);
+        return (int)R.brick_base + (bz * R.F.B[1] + by) * R.F.B[0] + bx;
+    }
     const int bx = min(cx / A.n[0], A.B[0] - 1);
     const int by = min(cy / A.n[1], A.B[1] - 1);
     const int bz = min(cz / A.n[2], A.B[2] - 1);
@@ -42,8 +37,9 @@ __global__ void bin_count_kernel(BinArgs A)
     __syncthreads();
     const uint32_t n = *A.src_count;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 a = reinterpret_cast<const float4 *>(A.src + i)[0];
         const int4 c = reinterpret_cast<const int4 *>(A.src + i)[1];
-        const int b = brick_id(A, c.x, c.y, c.z);
+        const int b = brick_key(A, __float_as_uint(a.w), c.x, c.y, c.z);
         if (local) atomicAdd(hist + b, 1u);
         else atomicAdd(A.brick_count + b, 1u);
     }
@@ -107,7 +103,7 @@ __global__ void bin_scatter_kernel(BinArgs A)
         if (!valid) continue;
         const int4 *s = reinterpret_cast<const int4 *>(A.src + i);
         const int4 r0 = s[0], r1 = s[1];
-        const int b = brick_id(A, r1.x, r1.y, r1.z);
+        const int b = brick_key(A, (uint32_t)r0.w, r1.x, r1.y, r1.z);
         const unsigned peers = __match_any_sync(vm, b);
         const int leader = __ffs(peers) - 1;
         uint32_t pos = 0;
@@ -155,11 +151,29 @@ sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_round
     return SG_OK;
 }
 
+sg_status launch_bin_args(const BinArgs &A, int sm_count, cudaStream_t s, bool in_graph, unsigned long long cond_handle,
+                          int mode)
+{
+    const int grid = sm_count * 2;
+    const size_t smem = A.nb <= 8192 ? sizeof(uint32_t) * A.nb : 0;
+    bin_count_kernel<<<grid, 512, smem, s>>>(A);
+    SG_CUDA(cudaGetLastError());
+    bin_scan_kernel<<<1, 1024, 0, s>>>(A);
+    SG_CUDA(cudaGetLastError());
+    bin_scatter_kernel<<<grid, 512, 0, s>>>(A);
+    SG_CUDA(cudaGetLastError());
+    ctrl_kernel<<<1, 32, 0, s>>>(A.ctrl, A.src_count, mode, (cudaGraphConditionalHandle)cond_handle, in_graph ? 1 : 0);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
 // mode 0: bin parked records (start of a call); mode 1: bin outgoing records.
 sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStream_t s, bool in_graph,
                      unsigned long long cond_handle, int mode)
 {
     BinArgs A;
+    A.line_req = nullptr;
+    A.reqs = nullptr;
     A.src = src;
     A.src_count = src_count;
     A.dst = t->q;
@@ -171,17 +185,7 @@ sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStrea
         A.B[a] = t->field->geom.B[a];
     }
     A.nb = t->nb;
-    const int grid = t->ctx->sm_count * 2;
-    const size_t smem = A.nb <= 8192 ? sizeof(uint32_t) * A.nb : 0;
-    bin_count_kernel<<<grid, 512, smem, s>>>(A);
-    SG_CUDA(cudaGetLastError());
-    bin_scan_kernel<<<1, 1024, 0, s>>>(A);
-    SG_CUDA(cudaGetLastError());
-    bin_scatter_kernel<<<grid, 512, 0, s>>>(A);
-    SG_CUDA(cudaGetLastError());
-    ctrl_kernel<<<1, 32, 0, s>>>(t->ctrl, src_count, mode, (cudaGraphConditionalHandle)cond_handle, in_graph ? 1 : 0);
-    SG_CUDA(cudaGetLastError());
-    return SG_OK;
+    return launch_bin_args(A, t->ctx->sm_count, s, in_graph, cond_handle, mode);
 }
 
 __global__ void iota_kernel(int32_t *dst, long long n)

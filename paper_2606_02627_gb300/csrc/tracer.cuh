@@ -32,6 +32,44 @@ struct LineParams {
 
 enum { EV_NONE = 0, EV_STOP = 1, EV_APPEND = 2, EV_PARK = 3 };
 
+// One request of a batch (device copy).  Its lines occupy the global line
+// slots [line_base, line_base + n_lines); its vertex slabs start at float
+// slab_base of the batch's slab pool, max_steps + 1 vertices per line.
+struct ReqDev {
+    DevField F;                  // slot 0 of the request's field
+    float dtc[3];
+    float eps;
+    float tie_cells;
+    float tie_eps_rel;
+    uint32_t max_steps;
+    uint32_t W;                  // max_steps + 1
+    long long slab_base;
+    uint32_t line_base;
+    uint32_t n_lines;
+    uint32_t brick_base;         // first global brick key of the request's field
+    int dtype;
+    double origin_d[3];          // the field's geometry in double (seed conversion)
+    double spacing_d[3];
+};
+
+// Arguments of the binning kernels (counting sort of particle records by
+// brick).  With line_req set, the key of a record is its request's
+// brick_base plus its brick in the request's field; otherwise its brick in
+// the single field (n, B).
+struct BinArgs {
+    const Particle *src;
+    uint32_t *src_count;
+    Particle *dst;
+    uint32_t *brick_count;
+    uint32_t *brick_cursor;
+    Ctrl *ctrl;
+    int n[3];
+    int B[3];
+    int nb;                      // number of keys
+    const uint32_t *line_req;    // batch: request of each line slot (else NULL)
+    const ReqDev *reqs;
+};
+
 }  // namespace sg
 
 struct sg_tracer {
@@ -86,6 +124,12 @@ sg_status launch_upload(sg_tracer *t, cudaStream_t s);
 sg_status launch_per_seed(sg_tracer *t, cudaStream_t s);
 sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStream_t s, bool in_graph,
                      unsigned long long cond_handle, int mode);
+sg_status launch_bin_args(const BinArgs &A, int sm_count, cudaStream_t s, bool in_graph, unsigned long long cond_handle,
+                          int mode);
+sg_status launch_compact_range(const uint32_t *len, long long n, const float *slab, long long W, const uint8_t *st_in,
+                               const float *mg_in, unsigned long long *block_sums, int64_t *dev_offsets,
+                               int64_t *totals, int64_t *offsets_out, float *vertices, uint8_t *status_out,
+                               float *margin_out, int sm_count, bool scan_only, cudaStream_t s);
 sg_status launch_round(sg_tracer *t, cudaStream_t s);
 sg_status prepare_round(sg_tracer *t);
 sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s);
