@@ -45,9 +45,9 @@ __device__ __forceinline__ int sample_brick(const DevField &F, const BrickRef<DT
         return SG_LINE_HALO;
     v = trilerp<DT, LAYOUT>(br.data, F, sx, sy, sz, f[0], f[1], f[2]);
     if (DT != SG_F32) {
-        v.x *= br.scale;
-        v.y *= br.scale;
-        v.z *= br.scale;
+        v.x = __fmul_rn(v.x, br.scale);
+        v.y = __fmul_rn(v.y, br.scale);
+        v.z = __fmul_rn(v.z, br.scale);
     }
     return 0;
 }
@@ -62,6 +62,11 @@ __device__ __forceinline__ float out_dist(const DevField &F, const int q[3], con
     return fmaxf(out_axis(q[0], g[0], F.nm1[0]), fmaxf(out_axis(q[1], g[1], F.nm1[1]), out_axis(q[2], g[2], F.nm1[2])));
 }
 
+// The products and sums below are written as explicit round-to-nearest
+// intrinsics so that no multiply is fused into a later add: every kernel that
+// inlines this step (tracer, Listing-1 form, request batch) then produces the
+// same bits for the same particle.
+//
 // One RK4 step of a particle owned by brick br.  On success updates (c, f)
 // and returns SG_LINE_ACTIVE; otherwise returns the stop status and leaves the
 // particle at P0.  margin is set for EXIT and STAGNANT.
@@ -72,12 +77,12 @@ __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3]
     float3 v;
     sample_brick<DT, LAYOUT>(F, br, c, f, v);            // P0 is owned: always inside the shell
     if (bad3(v)) return SG_LINE_NANFIELD;
-    const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    const float sp = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
     if (sp < eps) {
         margin = (eps - sp) / eps;
         return SG_LINE_STAGNANT;
     }
-    float k1[3] = {v.x * dtc[0], v.y * dtc[1], v.z * dtc[2]};
+    float k1[3] = {__fmul_rn(v.x, dtc[0]), __fmul_rn(v.y, dtc[1]), __fmul_rn(v.z, dtc[2])};
     int q[3];
     float g[3];
 #pragma unroll
@@ -88,7 +93,7 @@ __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3]
     }
     if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
     if (bad3(v)) return SG_LINE_NANFIELD;
-    float k2[3] = {v.x * dtc[0], v.y * dtc[1], v.z * dtc[2]};
+    float k2[3] = {__fmul_rn(v.x, dtc[0]), __fmul_rn(v.y, dtc[1]), __fmul_rn(v.z, dtc[2])};
 #pragma unroll
     for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k2[a], c[a], q[a], g[a]);
     if (!in_domain(F, q, g)) {
@@ -97,7 +102,7 @@ __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3]
     }
     if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
     if (bad3(v)) return SG_LINE_NANFIELD;
-    float k3[3] = {v.x * dtc[0], v.y * dtc[1], v.z * dtc[2]};
+    float k3[3] = {__fmul_rn(v.x, dtc[0]), __fmul_rn(v.y, dtc[1]), __fmul_rn(v.z, dtc[2])};
 #pragma unroll
     for (int a = 0; a < 3; ++a) locate(f[a], k3[a], c[a], q[a], g[a]);
     if (!in_domain(F, q, g)) {
@@ -106,10 +111,11 @@ __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3]
     }
     if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
     if (bad3(v)) return SG_LINE_NANFIELD;
-    const float k4[3] = {v.x * dtc[0], v.y * dtc[1], v.z * dtc[2]};
+    const float k4[3] = {__fmul_rn(v.x, dtc[0]), __fmul_rn(v.y, dtc[1]), __fmul_rn(v.z, dtc[2])};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float d = (k1[a] + k4[a] + 2.0f * (k2[a] + k3[a])) * (1.0f / 6.0f);
+        const float d = __fmul_rn(__fadd_rn(__fadd_rn(k1[a], k4[a]), __fmul_rn(2.0f, __fadd_rn(k2[a], k3[a]))),
+                                  1.0f / 6.0f);
         locate(f[a], d, c[a], q[a], g[a]);
     }
     if (!in_domain(F, q, g)) {
