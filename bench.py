@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--per-step", action="store_true", help="also time the one-launch-per-step kernel")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--schedule", default="", help="block,blocks_per_sm,steps_per_round")
-    ap.add_argument("--config", default="steady", choices=["steady", "streak"],
+    ap.add_argument("--requests", type=int, default=160, help="serve: requests in the Poisson stream")
+    ap.add_argument("--config", default="steady", choices=["steady", "streak", "serve"],
                     help="steady: brick-decomposed streamlines (the headline); streak: unsteady streaklines with "
                          "time slices streamed from page-locked host memory")
     ap.add_argument("--host-loop", action="store_true",
@@ -167,6 +168,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Seed stream of a rank: every rank traces its own seeds (weak scaling)."""
+    return base + 1000 * rank
+
+
+def reduce_over_ranks(ms: float, steps: int, dist, device):
+    """Whole-job timing across ranks: the slowest rank's time and the sum of
+    particle-steps (no collective on the data path: only these two numbers)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, steps
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([steps], dtype=torch.int64, device=device)
+    dist.all_reduce(s)
+    return float(t.item()), int(s.item())
+
+
 def cpu_oracle_rate(F_host, grid, seeds, dt, max_steps, seconds):
     """Oracle particle-steps/s on the host cores over a bounded prefix of the seeds."""
     import oracle
@@ -262,11 +281,71 @@ def run_streak(args, rank, world, local):
     print(json.dumps(out))
 
 
+def run_serve(args, rank, world, local):
+    """Batched serving of interactive seed placement: 8 resident fields ({64,128,256,512}^3 x {FP32, BF16},
+    synthetic turbulence seeds 4-11, CELL8 layout, 4x4x4 bricks), Poisson requests of 100 to 1M seeds (box or
+    rake), max steps 10-5000, admitted into one continuously batched persistent launch by free memory; the
+    arrival rate is 70 % of the capacity measured on the same requests arriving at once."""
+    import torch
+    from paper_2606_02627_gb300 import api, inputs, serving
+    from paper_2606_02627_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    ctx = api.Context(local)
+    fields = []
+    seed = 4
+    for n in (64, 128, 256, 512):
+        g = inputs.cube_grid(n)
+        F = inputs.turbulence_field(g, inputs.turbulence_modes(seed), device=dev)
+        probe = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(4, 4, 4), dtype="f32")
+        probe.set_global(F)
+        dt = args.h / probe.max_speed()
+        probe.close()
+        del probe
+        for dtype in ("f32", "bf16"):
+            fld = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(4, 4, 4), dtype=dtype, layout="cell8")
+            fld.set_global(F)
+            fields.append(serving.ResidentField(fld, g, dt))
+        del F
+        seed += 2
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info(dev)
+    slab = int(min(free * 0.6, 160e9))
+    srv = serving.Server(ctx, fields, max_lines=8 << 20, slab_bytes=slab, rounds_per_launch=4,
+                         max_requests=1024)
+    base = serving.make_requests(fields, args.requests, rate_hz=1.0, seed=4 + 1000 * rank)
+    # capacity: the same requests all arriving at once
+    burst = [serving.Request(r.idx, 0.0, r.field, r.seeds, r.max_steps, r.shape) for r in base]
+    srv.serve(burst)
+    cap = serving.summarize(burst)
+    rate = 0.7 * len(burst) / cap["makespan_s"]
+    reqs = [serving.Request(r.idx, r.arrival / rate, r.field, r.seeds, r.max_steps, r.shape) for r in base]
+    srv.serve(reqs)
+    st = serving.summarize(reqs)
+    out = {"metric": "p99 request latency (serving)", "value": st["p99_ms"], "unit": "ms", "n_gpus": 1,
+           "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "serving: 8 resident fields {64,128,256,512}^3 x {FP32,BF16} turbulence, Poisson "
+                                  f"requests ({args.requests}) of 100-1M seeds (box/rake), max steps 10-5000, "
+                                  f"rate = 70 % of measured capacity ({rate:.1f}/s)",
+                      "rounds_per_launch": 4, "slab_pool_bytes": slab},
+           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+           "particle_steps_per_s": st["particle_steps_per_s"], "particle_steps": st["particle_steps"],
+           "capacity": {"requests_per_s": len(burst) / cap["makespan_s"],
+                        "particle_steps_per_s": cap["particle_steps_per_s"]},
+           "queue_ms_p99": st["queue_ms_p99"]}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.config == "streak":
         return run_streak(args, rank, world, local)
+    if args.config == "serve":
+        return run_serve(args, rank, world, local)
     import numpy as np
     import torch
 
@@ -333,7 +412,7 @@ def main():
         b, bps, spr = (int(x) for x in args.schedule.split(","))
         sched = dict(block_size=b, blocks_per_sm=bps, steps_per_round=spr)
 
-    seeds_np = inputs.uniform_seeds(grid, args.seeds, 1 + 1000 * rank)
+    seeds_np = inputs.uniform_seeds(grid, args.seeds, rank_seed(1, rank))
     seeds_dev = torch.from_numpy(seeds_np).to(dev)
     seeds_pin = torch.from_numpy(seeds_np).pin_memory()
 
@@ -388,15 +467,7 @@ def main():
         e1.synchronize()
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / steps
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-            s = torch.tensor([float(tot)], device=dev)
-            dist.all_reduce(s)
-            tot_all = int(s.item())
-        else:
-            tot_all = tot
+        ms, tot_all = reduce_over_ranks(ms, tot, dist, dev)
         ok = tr.check(stream=stream)
         bytes_out = off.numel() * 8 + nv * 12 + nl
         return ms, tot, tot_all, bytes_out
