@@ -92,7 +92,7 @@ def peaks():
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("advect.cu", "common.cuh", "tracer.cuh"):
+    for f in ("advect.cu", "rk4.cuh", "common.cuh", "tracer.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2606_02627_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "tracer.cuh"
 
@@ -195,7 +196,19 @@ static size_t tracer_layout(const sg_field *f, const sg_tracer_params *p, int64_
         int64_t *off = (int64_t *)c.take(sizeof(int64_t) * (cap + 1));
         unsigned long long *bs = (unsigned long long *)c.take(sizeof(unsigned long long) * (cap / 4096 + 2));
         int64_t *tot = (int64_t *)c.take(sizeof(int64_t) * 4);
+        // two staging buffers for readback into host memory, each at least one line
+        size_t stage = (size_t)256 << 20;
+        const size_t line_bytes = sizeof(float) * 3 * (size_t)W;
+        if (stage < line_bytes) stage = line_bytes;
+        const size_t slab_bytes = sizeof(float) * 3 * (size_t)W * cap;
+        if (stage > slab_bytes) stage = slab_bytes > line_bytes ? slab_bytes : line_bytes;
+        stage = align_up(stage, 256);
+        float *st0 = (float *)c.take(stage);
+        float *st1 = (float *)c.take(stage);
         if (t) {
+            t->staging[0] = st0;
+            t->staging[1] = st1;
+            t->staging_bytes = stage;
             t->seeds = seeds;
             t->slab = slab;
             t->line_len = len;
@@ -282,6 +295,15 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
             delete t;
             return pst;
         }
+        cudaError_t ce = cudaStreamCreateWithFlags(&t->copy_stream, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
+            ce = cudaEventCreateWithFlags(&t->ev_gathered[k], cudaEventDisableTiming);
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t->ev_copied[k], cudaEventDisableTiming);
+        }
+        if (ce != cudaSuccess) {
+            sg_tracer_destroy(t);
+            return cuda_error(ce, "readback stream");
+        }
     }
     cudaError_t e = cudaMemset(t->ctrl ? (void *)t->ctrl : (void *)t->totals, 0,
                                t->ctrl ? sizeof(Ctrl) : sizeof(int64_t) * 4);
@@ -300,6 +322,11 @@ extern "C" sg_status sg_tracer_destroy(sg_tracer *t)
     if (!t) return SG_OK;
     if (t->exec) cudaGraphExecDestroy(t->exec);
     if (t->graph) cudaGraphDestroy(t->graph);
+    for (int k = 0; k < 2; ++k) {
+        if (t->ev_gathered[k]) cudaEventDestroy(t->ev_gathered[k]);
+        if (t->ev_copied[k]) cudaEventDestroy(t->ev_copied[k]);
+    }
+    if (t->copy_stream) cudaStreamDestroy(t->copy_stream);
     delete t;
     return SG_OK;
 }
@@ -611,6 +638,38 @@ extern "C" sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t
     if (line_source && t->n_seeds > 0) {
         st = launch_iota(line_source, t->n_seeds, s);
         if (st) return st;
+    }
+    if (vertices && pointer_kind(vertices) == PTR_PINNED && t->n_seeds > 0) {
+        // host destination: gather chunks of lines into device staging buffers
+        // and copy each to the host on the copy stream, overlapping the next
+        // chunk's gather (DMA copies beat kernel stores over the host link)
+        st = launch_gather_lines(t, offsets, nullptr, status, margin, s);
+        if (st) return st;
+        std::vector<int64_t> off((size_t)t->n_seeds + 1);
+        SG_CUDA(cudaMemcpyAsync(off.data(), t->offsets, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost, s));
+        SG_CUDA(cudaStreamSynchronize(s));
+        const long long cap_v = (long long)(t->staging_bytes / (3 * sizeof(float)));
+        long long a = 0;
+        int k = 0;
+        while (a < t->n_seeds) {
+            long long b = a + 1;
+            while (b < t->n_seeds && off[b + 1] - off[a] <= cap_v) ++b;
+            const int buf = k & 1;
+            SG_CUDA(cudaStreamWaitEvent(s, t->ev_copied[buf], 0));          // the buffer's last copy is done
+            st = launch_gather_chunk(t, a, b, off[a], t->staging[buf], s);
+            if (st) return st;
+            SG_CUDA(cudaEventRecord(t->ev_gathered[buf], s));
+            SG_CUDA(cudaStreamWaitEvent(t->copy_stream, t->ev_gathered[buf], 0));
+            const size_t bytes = sizeof(float) * 3 * (size_t)(off[b] - off[a]);
+            if (bytes)
+                SG_CUDA(cudaMemcpyAsync(vertices + 3 * off[a], t->staging[buf], bytes, cudaMemcpyDeviceToHost,
+                                        t->copy_stream));
+            SG_CUDA(cudaEventRecord(t->ev_copied[buf], t->copy_stream));
+            a = b;
+            ++k;
+        }
+        for (int buf = 0; buf < 2; ++buf) SG_CUDA(cudaStreamWaitEvent(s, t->ev_copied[buf], 0));
+        return SG_OK;
     }
     return launch_gather_lines(t, offsets, vertices, status, margin, s);
 }

@@ -128,7 +128,17 @@ __global__ void gather_lines_kernel(const float *__restrict__ slab, long long W,
         if (vertices) {
             const float *s = slab + i * W * 3;
             float *d = vertices + 3ll * off[i];
-            for (long long k = lane; k < cnt; k += 32) d[k] = s[k];
+            // eight independent loads in flight per lane before the stores:
+            // enough bytes in flight to stream at HBM rate
+            long long k = lane;
+            for (; k + 7 * 32 < cnt; k += 8 * 32) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldcs(s + k + u * 32);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) d[k + u * 32] = v[u];
+            }
+            for (; k < cnt; k += 32) d[k] = __ldcs(s + k);
         }
         if (lane == 0) {
             if (st_out) st_out[i] = st_in[i];
@@ -137,6 +147,38 @@ __global__ void gather_lines_kernel(const float *__restrict__ slab, long long W,
         }
     }
     if (off_out && blockIdx.x == 0 && threadIdx.x == 0) off_out[n] = off[n];
+}
+
+// Lines [a, b) into a staging buffer: line i lands at float 3 * (off[i] - base).
+__global__ void gather_chunk_kernel(const float *__restrict__ slab, long long W, const uint32_t *__restrict__ len,
+                                    const int64_t *__restrict__ off, long long a, long long b, long long base,
+                                    float *__restrict__ dst)
+{
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    for (long long i = a + warp; i < b; i += nwarps) {
+        const long long cnt = 3ll * len[i];
+        const float *s = slab + i * W * 3;
+        float *d = dst + 3ll * (off[i] - base);
+        long long k = lane;
+        for (; k + 7 * 32 < cnt; k += 8 * 32) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcs(s + k + u * 32);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d[k + u * 32] = v[u];
+        }
+        for (; k < cnt; k += 32) d[k] = __ldcs(s + k);
+    }
+}
+
+sg_status launch_gather_chunk(const sg_tracer *t, long long a, long long b, long long base, float *dst, cudaStream_t s)
+{
+    gather_chunk_kernel<<<t->ctx->sm_count * 8, 256, 0, s>>>(t->slab, (long long)t->p.max_steps + 1, t->line_len,
+                                                              t->offsets, a, b, base, dst);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
 }
 
 sg_status launch_scan_lengths(sg_tracer *t, cudaStream_t s)

@@ -99,6 +99,13 @@ struct sg_tracer {
     int64_t *totals;             // [0] vertices, [1] lines, [2] steps
     int64_t *host_totals;        // page-locked copy of totals
     bool scanned;
+    // readback into page-locked host memory: gather into device staging
+    // buffers, copy each to the host on a second stream (double buffered)
+    float *staging[2];
+    size_t staging_bytes;
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_gathered[2];
+    cudaEvent_t ev_copied[2];
     // streaklines
     int64_t n_release;
     int32_t births;              // births released so far
@@ -139,6 +146,7 @@ sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaSt
 sg_status launch_scan_lengths(sg_tracer *t, cudaStream_t s);
 sg_status launch_gather_lines(sg_tracer *t, int64_t *offsets, float *vertices, uint8_t *status, float *margin,
                               cudaStream_t s);
+sg_status launch_gather_chunk(const sg_tracer *t, long long a, long long b, long long base, float *dst, cudaStream_t s);
 sg_status launch_streak_release(sg_tracer *t, int birth, cudaStream_t s);
 sg_status launch_streak_scan(sg_tracer *t, cudaStream_t s);
 sg_status launch_streak_gather(sg_tracer *t, int64_t *offsets, float *vertices, uint8_t *status, float *margin,
