@@ -233,65 +233,69 @@ __device__ __forceinline__ float box_out(const DevField &F, float x, float y, fl
     return d;
 }
 
+// A grid-stride loop over the seeds: the grid sets how many seeds are in
+// flight per SM (as for the persistent kernel), each thread traces its seeds
+// one after the other.
 __global__ void __launch_bounds__(256) per_seed_kernel(const __grid_constant__ LineParams P)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n_lines) return;
     const float *Fg = reinterpret_cast<const float *>(P.F.data);
     const DevField &F = P.F;
-    // index-space seed, converted in double precision
-    const double sx = ((double)P.seeds[3 * i] - P.origin_d[0]) / P.spacing_d[0];
-    const double sy = ((double)P.seeds[3 * i + 1] - P.origin_d[1]) / P.spacing_d[1];
-    const double sz = ((double)P.seeds[3 * i + 2] - P.origin_d[2]) / P.spacing_d[2];
-    if (!(sx >= 0.0 && sx <= F.nm1[0] && sy >= 0.0 && sy <= F.nm1[1] && sz >= 0.0 && sz <= F.nm1[2])) {
-        P.line_len[i] = 0;
-        P.line_status[i] = SG_LINE_OUT;
-        P.line_margin[i] = INFINITY;
-        return;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n_lines;
+         i += (long long)gridDim.x * blockDim.x) {
+        // index-space seed, converted in double precision
+        const double sx = ((double)P.seeds[3 * i] - P.origin_d[0]) / P.spacing_d[0];
+        const double sy = ((double)P.seeds[3 * i + 1] - P.origin_d[1]) / P.spacing_d[1];
+        const double sz = ((double)P.seeds[3 * i + 2] - P.origin_d[2]) / P.spacing_d[2];
+        if (!(sx >= 0.0 && sx <= F.nm1[0] && sy >= 0.0 && sy <= F.nm1[1] && sz >= 0.0 && sz <= F.nm1[2])) {
+            P.line_len[i] = 0;
+            P.line_status[i] = SG_LINE_OUT;
+            P.line_margin[i] = INFINITY;
+            continue;
+        }
+        float px = (float)sx, py = (float)sy, pz = (float)sz;
+        float *out = P.slab + (long long)i * P.W * 3;
+        out[0] = P.seeds[3 * i];
+        out[1] = P.seeds[3 * i + 1];
+        out[2] = P.seeds[3 * i + 2];
+        uint32_t step = 0;
+        int st = SG_LINE_MAXSTEPS;
+        float margin = INFINITY;
+        while (step < P.max_steps) {
+            float3 v = sample_global(Fg, F, px, py, pz);
+            if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
+            const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+            if (sp < P.eps) { st = SG_LINE_STAGNANT; margin = (P.eps - sp) / P.eps; break; }
+            const float k1x = v.x * P.dtc[0], k1y = v.y * P.dtc[1], k1z = v.z * P.dtc[2];
+            float qx = px + 0.5f * k1x, qy = py + 0.5f * k1y, qz = pz + 0.5f * k1z;
+            if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
+            v = sample_global(Fg, F, qx, qy, qz);
+            if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
+            const float k2x = v.x * P.dtc[0], k2y = v.y * P.dtc[1], k2z = v.z * P.dtc[2];
+            qx = px + 0.5f * k2x; qy = py + 0.5f * k2y; qz = pz + 0.5f * k2z;
+            if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
+            v = sample_global(Fg, F, qx, qy, qz);
+            if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
+            const float k3x = v.x * P.dtc[0], k3y = v.y * P.dtc[1], k3z = v.z * P.dtc[2];
+            qx = px + k3x; qy = py + k3y; qz = pz + k3z;
+            if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
+            v = sample_global(Fg, F, qx, qy, qz);
+            if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
+            const float k4x = v.x * P.dtc[0], k4y = v.y * P.dtc[1], k4z = v.z * P.dtc[2];
+            qx = px + (k1x + k4x + 2.0f * (k2x + k3x)) * (1.0f / 6.0f);
+            qy = py + (k1y + k4y + 2.0f * (k2y + k3y)) * (1.0f / 6.0f);
+            qz = pz + (k1z + k4z + 2.0f * (k2z + k3z)) * (1.0f / 6.0f);
+            if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
+            px = qx; py = qy; pz = qz;
+            ++step;
+            float *o = out + 3ll * step;
+            o[0] = fmaf(F.spacing[0], px, F.origin[0]);
+            o[1] = fmaf(F.spacing[1], py, F.origin[1]);
+            o[2] = fmaf(F.spacing[2], pz, F.origin[2]);
+        }
+        P.line_len[i] = step + 1;
+        P.line_status[i] = stop_code(P, st, margin);
+        P.line_margin[i] = margin;
     }
-    float px = (float)sx, py = (float)sy, pz = (float)sz;
-    float *out = P.slab + (long long)i * P.W * 3;
-    out[0] = P.seeds[3 * i];
-    out[1] = P.seeds[3 * i + 1];
-    out[2] = P.seeds[3 * i + 2];
-    uint32_t step = 0;
-    int st = SG_LINE_MAXSTEPS;
-    float margin = INFINITY;
-    while (step < P.max_steps) {
-        float3 v = sample_global(Fg, F, px, py, pz);
-        if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-        const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
-        if (sp < P.eps) { st = SG_LINE_STAGNANT; margin = (P.eps - sp) / P.eps; break; }
-        const float k1x = v.x * P.dtc[0], k1y = v.y * P.dtc[1], k1z = v.z * P.dtc[2];
-        float qx = px + 0.5f * k1x, qy = py + 0.5f * k1y, qz = pz + 0.5f * k1z;
-        if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
-        v = sample_global(Fg, F, qx, qy, qz);
-        if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-        const float k2x = v.x * P.dtc[0], k2y = v.y * P.dtc[1], k2z = v.z * P.dtc[2];
-        qx = px + 0.5f * k2x; qy = py + 0.5f * k2y; qz = pz + 0.5f * k2z;
-        if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
-        v = sample_global(Fg, F, qx, qy, qz);
-        if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-        const float k3x = v.x * P.dtc[0], k3y = v.y * P.dtc[1], k3z = v.z * P.dtc[2];
-        qx = px + k3x; qy = py + k3y; qz = pz + k3z;
-        if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
-        v = sample_global(Fg, F, qx, qy, qz);
-        if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-        const float k4x = v.x * P.dtc[0], k4y = v.y * P.dtc[1], k4z = v.z * P.dtc[2];
-        qx = px + (k1x + k4x + 2.0f * (k2x + k3x)) * (1.0f / 6.0f);
-        qy = py + (k1y + k4y + 2.0f * (k2y + k3y)) * (1.0f / 6.0f);
-        qz = pz + (k1z + k4z + 2.0f * (k2z + k3z)) * (1.0f / 6.0f);
-        if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
-        px = qx; py = qy; pz = qz;
-        ++step;
-        float *o = out + 3ll * step;
-        o[0] = fmaf(F.spacing[0], px, F.origin[0]);
-        o[1] = fmaf(F.spacing[1], py, F.origin[1]);
-        o[2] = fmaf(F.spacing[2], pz, F.origin[2]);
-    }
-    P.line_len[i] = step + 1;
-    P.line_status[i] = stop_code(P, st, margin);
-    P.line_margin[i] = margin;
 }
 
 // ------------------------------------------------------------------ seed upload
@@ -361,8 +365,10 @@ sg_status launch_per_seed(sg_tracer *t, cudaStream_t s)
 {
     LineParams P = line_params(t);
     if (t->n_seeds == 0) return SG_OK;
-    const int block = t->block > 0 ? t->block : 256;
-    per_seed_kernel<<<(unsigned)((t->n_seeds + block - 1) / block), block, 0, s>>>(P);
+    const int block = t->block;
+    long long grid = (t->n_seeds + block - 1) / block;
+    if (grid > t->grid) grid = t->grid;
+    per_seed_kernel<<<(unsigned)grid, block, 0, s>>>(P);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }
