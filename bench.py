@@ -9,11 +9,11 @@ one-cell ghost shell and encoded to the benchmarked storage type; 1M seeds
 with h = 0.5 cell runs to max 2000 steps (exit / |v| < 1e-6 / cap) with
 cross-brick hand-off queues; the lines are compacted to CSR.
 
-`value` is the persistent form on the 16-bit-footprint precision field: 21-bit
-fixed point, three components in the 8 bytes a BF16 sample takes, per-brick
-scale (the BF16 and FP16 fields are as fast but their 8- and 11-bit mantissas
-miss the 5e-2-cell error bound on this flow).  The BF16, FP16 and FP32
-persistent forms, the plain FP32 per-seed kernel and (optionally) the
+`value` is the persistent form on the FP32 field (the samples as given, in
+8-corner cell records), run by the decoupled-lane kernel.  The compact
+storage forms (FX21: 21-bit fixed point, three components in 8 bytes with a
+per-brick scale; BF16; FP16), the same FP32 field under the lockstep
+persistent kernel, the plain FP32 per-seed kernel and (optionally) the
 one-launch-per-step kernel of Listing 1 are timed in the same run under
 `variants`.  `e2e` repeats the headline through the C ABI with the seeds
 copied from page-locked host memory and the CSR lines written to page-locked
@@ -57,7 +57,9 @@ def parse():
     ap.add_argument("--seeds", type=int, default=1 << 20)
     ap.add_argument("--max-steps", type=int, default=2000)
     ap.add_argument("--h", type=float, default=0.5)
-    ap.add_argument("--dtype", default="fx21", choices=["f32", "bf16", "f16", "fx21"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16", "fx21"])
+    ap.add_argument("--kernel", default="persistent", choices=["persistent", "lockstep"],
+                    help="headline kernel: decoupled lanes (persistent, CELL8) or lanes in lockstep")
     ap.add_argument("--layout", default="cell8")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--per-step", action="store_true", help="also time the one-launch-per-step kernel")
@@ -97,10 +99,11 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_step(dtype):
-    """DRAM bytes per particle-step of the round kernel from the committed ncu
-    summary, or None if it is missing or the kernel changed since."""
-    p = os.path.join(ROOT, "profiles", f"round_kernel_{dtype}_traffic.txt")
+def traffic_per_step(dtype, tag):
+    """DRAM bytes per particle-step of the advection kernel (tag "async": the
+    decoupled-lane kernel, "lockstep": lanes in lockstep) from the committed
+    ncu summary, or None if it is missing or the kernel changed since."""
+    p = os.path.join(ROOT, "profiles", f"round_{tag}_{dtype}_traffic.txt")
     if not os.path.exists(p):
         return None
     kv = {}
@@ -358,7 +361,8 @@ def main():
                           f"max {args.max_steps} steps",
               "field": f"{n}^3", "bricks": "4x4x4", "seeds_per_gpu": args.seeds, "max_steps": args.max_steps,
               "h_cells": args.h, "field_storage": args.dtype, "layout": args.layout,
-              "l2": "inputs larger than L2 (field 1.6 GB, bricks 0.9-1.8 GB, slabs 24 GB)",
+              "l2": "inputs larger than L2 (field 1.6 GB; cell records 18 GB FP32, 9 GB 8-byte formats; "
+                    "slabs 24 GB)",
               "parallelism": f"replicas x{world} (seeds per rank, field replicated)"}
 
     if args.impl == "reference":
@@ -421,7 +425,7 @@ def main():
                         bricks=(1, 1, 1) if layout == "global" else (4, 4, 4), dtype=dtype, layout=layout)
         fld.set_global(F, stream=stream)
         tr = api.Tracer(ctx, fld, capacity=args.seeds, dt=dt, max_steps=args.max_steps, kernel=kernel,
-                        **(sched if kernel == "persistent" else {}))
+                        **(sched if kernel in ("persistent", "lockstep") else {}))
         return fld, tr
 
     # dt from the FP32 field's largest speed: every step is at most h cells
@@ -479,8 +483,8 @@ def main():
     except Exception:
         pass
 
-    # headline: the chosen storage type, persistent form
-    fld, tr = make(args.dtype, args.layout, "persistent")
+    # headline: the chosen storage type and persistent kernel
+    fld, tr = make(args.dtype, args.layout, args.kernel)
     if args.once:
         one_step(fld, tr, None, None, None, seeds_dev)
         stream.synchronize()
@@ -502,10 +506,14 @@ def main():
     hbm, peak_kind = peaks()
     bps = GATHER_BYTES[args.dtype]
     achieved = ksteps * bps / (kms / 1e3) / 1e9
-    tps = traffic_per_step(args.dtype)
+    tag = "async" if args.kernel == "persistent" and args.layout == "cell8" else "lockstep"
+    tps = traffic_per_step(args.dtype, tag)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": (tps * ksteps / launches) if tps else None,
-                "kernel": "round_kernel (persistent advection)", "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel": ("round_async_kernel (persistent advection, decoupled lanes)"
+                           if args.kernel == "persistent" and args.layout == "cell8"
+                           else "round_kernel (persistent advection, lanes in lockstep)"),
+                "peak_source": f"{peak_kind} hbm_gbs",
                 "model": f"gather bytes: 4 samples x 8 corners x 3 comps x elem + 12 B vertex = {bps} B "
                          f"per particle-step (L1/L2 hits counted at HBM price)",
                 "kernel_ms_per_launch": kms / launches, "launches": launches,
@@ -522,6 +530,8 @@ def main():
     if not args.no_variants:
         runs = [(f"{d}_persistent", d, args.layout, "persistent") for d in ("fx21", "f16", "bf16", "f32")
                 if d != args.dtype]
+        other = "lockstep" if args.kernel == "persistent" else "persistent"
+        runs.append((f"{args.dtype}_{other}", args.dtype, args.layout, other))
         runs.append(("f32_per_seed", "f32", "global", "per_seed"))
         if args.per_step:
             runs.append(("f32_per_step", "f32", args.layout, "per_step"))
@@ -532,8 +542,8 @@ def main():
                               "field_storage": dtp, "kernel": ker}
             del t2, f2
             torch.cuda.empty_cache()
-        variants[f"{args.dtype}_persistent"] = {"value": value, "ms_per_step": ms, "particle_steps": tot,
-                                                "field_storage": args.dtype, "kernel": "persistent"}
+        variants[f"{args.dtype}_{args.kernel}"] = {"value": value, "ms_per_step": ms, "particle_steps": tot,
+                                                   "field_storage": args.dtype, "kernel": args.kernel}
 
     cpu = None
     if rank == 0:

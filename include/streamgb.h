@@ -99,8 +99,14 @@ enum {
                                   per-brick queues; rounds run as one CUDA graph  */
     SG_KERNEL_PER_SEED = 1,    /* one thread per seed to termination on a global
                                   FP32 field (layout SG_FIELD_GLOBAL only)         */
-    SG_KERNEL_PER_STEP = 2     /* Listing 1: one launch per advection step, one
+    SG_KERNEL_PER_STEP = 2,    /* Listing 1: one launch per advection step, one
                                   thread per particle, forwarding between launches */
+    SG_KERNEL_LOCKSTEP = 3     /* the persistent kernel with the lanes of a warp in
+                                  lockstep (every sample a load the warp waits
+                                  for).  SG_KERNEL_PERSISTENT on a CELL8 field
+                                  decouples the lanes instead: each holds its
+                                  current cell record and fetches the next one
+                                  asynchronously; both give the same bits.    */
 };
 
 typedef struct sg_context sg_context;

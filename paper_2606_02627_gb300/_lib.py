@@ -28,7 +28,7 @@ ERR_NAMES = {0: "SG_OK", -1: "SG_ERR_INVALID_ARG", -2: "SG_ERR_OOM", -3: "SG_ERR
 SG_F32, SG_BF16, SG_F16, SG_FX21 = 0, 1, 2, 3
 SG_LAYOUT_LINEAR, SG_LAYOUT_TILED4, SG_LAYOUT_CELL8, SG_FIELD_GLOBAL = 0, 1, 2, 16
 SG_STREAMLINE, SG_STREAKLINE = 0, 1
-SG_KERNEL_PERSISTENT, SG_KERNEL_PER_SEED, SG_KERNEL_PER_STEP = 0, 1, 2
+SG_KERNEL_PERSISTENT, SG_KERNEL_PER_SEED, SG_KERNEL_PER_STEP, SG_KERNEL_LOCKSTEP = 0, 1, 2, 3
 SG_LINE_ACTIVE, SG_LINE_MAXSTEPS, SG_LINE_EXIT, SG_LINE_STAGNANT = 0, 1, 2, 3
 SG_LINE_NANFIELD, SG_LINE_OUT, SG_LINE_HALO, SG_LINE_TIE = 4, 5, 6, 0x80
 

@@ -17,7 +17,8 @@ from ._lib import call
 DTYPES = {"f32": L.SG_F32, "bf16": L.SG_BF16, "f16": L.SG_F16, "fx21": L.SG_FX21}
 LAYOUTS = {"linear": L.SG_LAYOUT_LINEAR, "tiled4": L.SG_LAYOUT_TILED4, "cell8": L.SG_LAYOUT_CELL8,
            "global": L.SG_FIELD_GLOBAL}
-KERNELS = {"persistent": L.SG_KERNEL_PERSISTENT, "per_seed": L.SG_KERNEL_PER_SEED, "per_step": L.SG_KERNEL_PER_STEP}
+KERNELS = {"persistent": L.SG_KERNEL_PERSISTENT, "per_seed": L.SG_KERNEL_PER_SEED, "per_step": L.SG_KERNEL_PER_STEP,
+           "lockstep": L.SG_KERNEL_LOCKSTEP}
 STATUS_NAMES = {0: "ACTIVE", 1: "MAXSTEPS", 2: "EXIT", 3: "STAGNANT", 4: "NANFIELD", 5: "OUT", 6: "HALO"}
 
 

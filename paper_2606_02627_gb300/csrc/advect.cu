@@ -28,9 +28,9 @@ __device__ __forceinline__ void write_vertex(const LineParams &P, uint32_t line,
                                              const float f[3])
 {
     float *o = P.slab + ((long long)line * P.W + step) * 3;
-    o[0] = fmaf(P.F.spacing[0], (float)c[0] + f[0], P.F.origin[0]);
-    o[1] = fmaf(P.F.spacing[1], (float)c[1] + f[1], P.F.origin[1]);
-    o[2] = fmaf(P.F.spacing[2], (float)c[2] + f[2], P.F.origin[2]);
+    st_na(o, fmaf(P.F.spacing[0], (float)c[0] + f[0], P.F.origin[0]));
+    st_na(o + 1, fmaf(P.F.spacing[1], (float)c[1] + f[1], P.F.origin[1]));
+    st_na(o + 2, fmaf(P.F.spacing[2], (float)c[2] + f[2], P.F.origin[2]));
 }
 
 __device__ __forceinline__ uint8_t stop_code(const LineParams &P, int st, float margin)
@@ -129,6 +129,217 @@ __global__ void __launch_bounds__(256) round_kernel(const __grid_constant__ Line
         }
         if (ev != EV_NONE) active = false;
     }
+}
+
+// ------------------------------------------------------------------ persistent round kernel, decoupled lanes
+
+// Consecutive passes a lane may wait for one record copy (each pass of a warp
+// takes at least ~100 cycles: well over a second in all).
+constexpr unsigned COPY_WAIT_PASSES = 1u << 24;
+
+// The same round as round_kernel for the CELL8 layout, with the lanes of a
+// warp no longer waiting for one another at each sample.  In round_kernel
+// every one of the four samples of a step is a load that the whole warp
+// waits for, so the warp runs at the pace of its slowest lane: at nearly
+// every sample some lane has just entered a cell whose record is not in L1.
+// Here each lane keeps the record of the cell of its current sample point in
+// its own shared-memory slot and runs one RK4 stage per pass of the warp's
+// loop.  When a stage point falls in another cell, the lane starts an
+// asynchronous copy of that record (cp.async through L1) into its slot,
+// completing on its own mbarrier, and sits out the passes until the copy has
+// landed while the other lanes go on.  The stage arithmetic is
+// rk4_bricked's, operation for operation, so both kernels produce the same
+// bits.
+template <int DT>
+__global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant__ LineParams P)
+{
+    constexpr int NCH = Record<DT>::chunks;
+    extern __shared__ uint4 slots[];                       // [NCH][blockDim] chunks, then blockDim barriers
+    const unsigned tid = threadIdx.x, nthr = blockDim.x;
+    const unsigned lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + NCH * nthr) + tid);
+    const uint32_t slot = smem_addr(slots + tid);
+    mbar_init(bar, 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+
+    const DevField &F = P.F;
+    const uint32_t q_count = P.ctrl->q_count;
+    const uint32_t horizon = P.ctrl->horizon;
+    bool active = false, pending = false;
+    bool drained = q_count == 0;
+    uint32_t drain_left = P.drain_steps;
+    unsigned parity = 0, waited = 0;
+    int c[3] = {0, 0, 0}, q[3] = {0, 0, 0};               // P0 and the current sample point
+    float f[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};
+    float k1[3] = {0.f, 0.f, 0.f}, k2[3] = {0.f, 0.f, 0.f}, k3[3] = {0.f, 0.f, 0.f};
+    float ds[3] = {0.f, 0.f, 0.f};
+    uint32_t line = 0, step = 0, here = 0, stage = 0;
+    uint32_t held = 0xffffffffu, wanted = 0;              // cell of the record in the slot / in flight
+    BrickRef<DT> br;
+    br.data = nullptr;
+    br.scale = 1.0f;
+    for (int a = 0; a < 3; ++a) br.lo[a] = br.hi[a] = 0;
+
+    // the record of sample point q into the slot, unless it is there already
+    auto fetch = [&]() {
+        const int sx = q[0] - br.lo[0] + 1, sy = q[1] - br.lo[1] + 1, sz = q[2] - br.lo[2] + 1;
+        const uint32_t cell = (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
+        if (cell != held) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(br.data + (long long)cell * 8);
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) cp_async16(slot + k * nthr * 16u, src + k);
+            cp_async_arrive(bar);
+            held = 0xffffffffu;
+            wanted = cell;
+            pending = true;
+            waited = 0;
+        }
+    };
+
+    while (true) {
+        const unsigned need = __ballot_sync(SG_FULL_MASK, !active);
+        if (need && !drained) {
+            const int leader = __ffs(need) - 1;
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(&P.ctrl->q_head, (uint32_t)__popc(need));
+            base = __shfl_sync(SG_FULL_MASK, base, leader);
+            if (base + (uint32_t)__popc(need) >= q_count) drained = true;
+            if (!active) {
+                const uint32_t my = base + __popc(need & lt);
+                if (my < q_count) {
+                    load_particle(P.q + my, c, f, line, step);
+                    brick_of<DT>(F, c, br);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        ds[a] = (DT == SG_F32) ? P.dtc[a] : __fmul_rn(P.dtc[a], br.scale);
+                        q[a] = c[a];
+                        g[a] = f[a];
+                    }
+                    active = true;
+                    here = 0;
+                    stage = 0;
+                    held = 0xffffffffu;            // another brick: the slot's record is stale
+                    fetch();
+                }
+            }
+        }
+        if (__ballot_sync(SG_FULL_MASK, active) == 0) break;
+        if (drained) {
+            if (drain_left == 0) here = P.steps_per_round;
+            else --drain_left;
+        }
+        bool gave_up = false;
+        if (pending) {
+            if (mbar_done(bar, parity)) {
+                held = wanted;
+                parity ^= 1u;
+                pending = false;
+            } else if (++waited >= COPY_WAIT_PASSES) {
+                // the particle is dropped and the call fails; the warp takes
+                // no other particle while this lane's barrier may still complete
+                atomicOr(&P.ctrl->err, CTRL_ERR_TIMEOUT);
+                active = false;
+                pending = false;
+                gave_up = true;
+            }
+        }
+        if (__any_sync(SG_FULL_MASK, gave_up)) drained = true;
+
+        int ev = EV_NONE, st = SG_LINE_ACTIVE;
+        float margin = INFINITY;
+        bool run = active && !pending;
+        if (run && stage == 0) {
+            if (step >= horizon) {
+                if (step >= P.max_steps) {
+                    ev = EV_STOP;
+                    st = SG_LINE_MAXSTEPS;
+                } else {
+                    ev = EV_PARK;
+                }
+                run = false;
+            } else if (here >= P.steps_per_round) {
+                ev = EV_APPEND;
+                run = false;
+            }
+        }
+        if (run) {
+            // one stage, the same instructions at every stage (the lanes of a
+            // warp are at different stages): sample, k = v dt/h, and the next
+            // point P0 + w k (stages 0-2) or P' (stage 3)
+            Record<DT> R;
+#pragma unroll
+            for (int k = 0; k < NCH; ++k) R.r[k] = slots[k * nthr + tid];
+            bool bad;
+            const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad);
+            float sp = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
+            if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
+            const float k[3] = {__fmul_rn(v.x, ds[0]), __fmul_rn(v.y, ds[1]), __fmul_rn(v.z, ds[2])};
+            const bool last = stage == 3;
+            const float w = stage < 2 ? 0.5f : 1.0f;   // P1, P2 = P0 + k/2; P3 = P0 + k3
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float fin =
+                    __fmul_rn(__fadd_rn(__fadd_rn(k1[a], k[a]), __fmul_rn(2.0f, __fadd_rn(k2[a], k3[a]))), 1.0f / 6.0f);
+                locate(f[a], last ? fin : w * k[a], c[a], q[a], g[a]);
+                k1[a] = stage == 0 ? k[a] : k1[a];
+                k2[a] = stage == 1 ? k[a] : k2[a];
+                k3[a] = stage == 2 ? k[a] : k3[a];
+            }
+            if (bad) {
+                st = SG_LINE_NANFIELD;
+            } else if (stage == 0 && sp < P.eps) {
+                margin = (P.eps - sp) / P.eps;
+                st = SG_LINE_STAGNANT;
+            } else if (!in_domain(F, q, g)) {
+                margin = out_dist(F, q, g);
+                st = SG_LINE_EXIT;
+            } else if (!last && ((unsigned)(q[0] - br.lo[0] + 1) > (unsigned)(F.S[0] - 2) ||
+                                 (unsigned)(q[1] - br.lo[1] + 1) > (unsigned)(F.S[1] - 2) ||
+                                 (unsigned)(q[2] - br.lo[2] + 1) > (unsigned)(F.S[2] - 2))) {
+                st = SG_LINE_HALO;
+            }
+            bool go = st == SG_LINE_ACTIVE;
+            if (!go) ev = EV_STOP;
+            if (go && last) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    c[a] = q[a];
+                    f[a] = g[a];
+                }
+                ++step;
+                ++here;
+                write_vertex(P, line, step, c, f);
+                if (step >= horizon) {
+                    ev = step >= P.max_steps ? EV_STOP : EV_PARK;
+                    st = step >= P.max_steps ? SG_LINE_MAXSTEPS : st;
+                    go = false;
+                } else if (c[0] < br.lo[0] || c[0] >= br.hi[0] || c[1] < br.lo[1] || c[1] >= br.hi[1] ||
+                           c[2] < br.lo[2] || c[2] >= br.hi[2]) {
+                    ev = EV_APPEND;               // destinationID(new position) != this brick
+                    go = false;
+                } else {
+                    go = here < P.steps_per_round;   // else re-queued at the next pass, no fetch
+                }
+            }
+            stage = last ? 0 : stage + 1;
+            if (go) fetch();                      // the record of the next sample point q
+        }
+        if (__any_sync(SG_FULL_MASK, ev != EV_NONE)) {
+            warp_append(ev == EV_APPEND, P.o, &P.ctrl->o_count, c, f, line, step);
+            warp_append(ev == EV_PARK, P.park, &P.ctrl->p_count, c, f, line, step);
+            if (ev == EV_STOP) {
+                P.line_len[line] = step + 1;
+                P.line_status[line] = stop_code(P, st, margin);
+                P.line_margin[line] = margin;
+            } else if (ev == EV_PARK) {
+                P.line_len[line] = step + 1;
+            }
+            if (ev != EV_NONE) active = false;
+        }
+    }
+    cp_async_wait_all();    // only after a copy wait ran out can one be in flight
 }
 
 // ------------------------------------------------------------------ Listing 1: one launch per step
@@ -288,9 +499,9 @@ __global__ void __launch_bounds__(256) per_seed_kernel(const __grid_constant__ L
             px = qx; py = qy; pz = qz;
             ++step;
             float *o = out + 3ll * step;
-            o[0] = fmaf(F.spacing[0], px, F.origin[0]);
-            o[1] = fmaf(F.spacing[1], py, F.origin[1]);
-            o[2] = fmaf(F.spacing[2], pz, F.origin[2]);
+            st_na(o, fmaf(F.spacing[0], px, F.origin[0]));
+            st_na(o + 1, fmaf(F.spacing[1], py, F.origin[1]));
+            st_na(o + 2, fmaf(F.spacing[2], pz, F.origin[2]));
         }
         P.line_len[i] = step + 1;
         P.line_status[i] = stop_code(P, st, margin);
@@ -373,20 +584,43 @@ sg_status launch_per_seed(sg_tracer *t, cudaStream_t s)
     return SG_OK;
 }
 
+// The decoupled-lane form runs for the CELL8 layout; SG_KERNEL_LOCKSTEP (and
+// the other layouts) take round_kernel.
+static bool use_async(int kernel, int layout) { return kernel == SG_KERNEL_PERSISTENT && layout == SG_LAYOUT_CELL8; }
+
+template <int DT>
+static size_t async_smem(int block)
+{
+    return (size_t)block * (Record<DT>::chunks * 16 + 8);
+}
+
 template <int DT, int LAYOUT>
 static void launch_round_t(const LineParams &P, int grid, int block, int kernel, cudaStream_t s)
 {
     if (kernel == SG_KERNEL_PER_STEP) per_step_kernel<DT, LAYOUT><<<grid, block, 0, s>>>(P);
+    else if (use_async(kernel, LAYOUT)) round_async_kernel<DT><<<grid, block, async_smem<DT>(block), s>>>(P);
     else round_kernel<DT, LAYOUT><<<grid, block, 0, s>>>(P);
 }
 
-// The advection kernels use no shared memory: ask for the whole unified
-// L1/shared array as L1, which holds the particles' current cell records.
+// The lockstep and Listing-1 kernels use no shared memory: ask for the whole
+// unified L1/shared array as L1, which holds the particles' current cell
+// records.  The decoupled-lane kernel asks for the smallest shared part that
+// holds its record slots at the tracer's blocks per SM.
 template <int DT, int LAYOUT>
-static cudaError_t prefer_l1_t(int kernel)
+static cudaError_t prefer_l1_t(int kernel, int block, int blocks_per_sm)
 {
     if (kernel == SG_KERNEL_PER_STEP)
         return cudaFuncSetAttribute(per_step_kernel<DT, LAYOUT>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    if (use_async(kernel, LAYOUT)) {
+        const size_t per_block = async_smem<DT>(block);
+        cudaError_t e = cudaFuncSetAttribute(round_async_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)per_block);
+        if (e != cudaSuccess) return e;
+        const size_t total = per_block * (size_t)blocks_per_sm + 1024 * (size_t)blocks_per_sm;
+        int pct = (int)((total * 100 + 228 * 1024 - 1) / (228 * 1024));
+        if (pct > 100) pct = 100;
+        return cudaFuncSetAttribute(round_async_kernel<DT>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    }
     return cudaFuncSetAttribute(round_kernel<DT, LAYOUT>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
 }
 
@@ -399,7 +633,10 @@ sg_status prepare_round(sg_tracer *t)
     cudaError_t e = cudaSuccess;
     with_dtype(t->field->desc.dtype, [&](auto D) {
         with_layout(t->field->desc.layout,
-                    [&](auto Lay) { e = prefer_l1_t<decltype(D)::value, decltype(Lay)::value>(t->p.kernel); });
+                    [&](auto Lay) {
+                        e = prefer_l1_t<decltype(D)::value, decltype(Lay)::value>(t->p.kernel, t->block,
+                                                                                 t->grid / t->ctx->sm_count);
+                    });
     });
     SG_CUDA(e);
     return SG_OK;

@@ -157,7 +157,7 @@ static sg_status check_params(const sg_field *f, const sg_tracer_params *p)
     if (p->mode == SG_STREAMLINE) {
         SG_CHECK(p->max_steps >= 0 && p->max_steps < (1 << 27), SG_ERR_INVALID_ARG, "max_steps out of range");
         SG_CHECK(p->kernel == SG_KERNEL_PERSISTENT || p->kernel == SG_KERNEL_PER_SEED ||
-                     p->kernel == SG_KERNEL_PER_STEP,
+                     p->kernel == SG_KERNEL_PER_STEP || p->kernel == SG_KERNEL_LOCKSTEP,
                  SG_ERR_INVALID_ARG, "bad kernel %d", p->kernel);
         if (p->kernel == SG_KERNEL_PER_SEED)
             SG_CHECK(f->desc.layout == SG_FIELD_GLOBAL, SG_ERR_UNSUPPORTED,
@@ -285,9 +285,14 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
     if (t->p.steps_per_round <= 0) t->p.steps_per_round = 128;
     if (t->p.drain_steps <= 0) t->p.drain_steps = 0x7fffffff;
     t->block = p->block_size > 0 ? p->block_size : 256;
-    // default: 512 resident threads per SM; more particles per SM thrash the L1
-    // that holds their cell records (measured on GB300)
-    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : (512 + t->block - 1) / t->block;
+    // default resident threads per SM (measured on GB300): 512 for the kernels
+    // that read every sample through L1, where more particles per SM thrash the
+    // L1 that holds their cell records; 768 for the decoupled-lane kernel,
+    // whose records sit in shared memory and which is bound by instruction
+    // issue instead
+    const bool decoupled = p->kernel == SG_KERNEL_PERSISTENT && f->desc.layout == SG_LAYOUT_CELL8;
+    const int threads_per_sm = decoupled ? 768 : 512;
+    const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : (threads_per_sm + t->block - 1) / t->block;
     t->grid = ctx->sm_count * (per_sm > 0 ? per_sm : 1);
     if (t->p.mode == SG_STREAMLINE) {
         sg_status pst = prepare_round(t);
@@ -552,6 +557,10 @@ extern "C" sg_status sg_tracer_step(sg_tracer *t, int32_t n_steps, int32_t *any_
         SG_CUDA(cudaMemcpyAsync(&c, t->ctrl, sizeof c, cudaMemcpyDeviceToHost, s));
         SG_CUDA(cudaStreamSynchronize(s));
         *any_active = (t->n_seeds > 0 && c.p_count > 0) ? 1 : 0;
+        if (c.err & CTRL_ERR_TIMEOUT) {
+            set_error("a record copy of the advection kernel did not complete in time");
+            return SG_ERR_TIMEOUT;
+        }
         if (c.err & CTRL_ERR_ROUND_LIMIT) {
             set_error("the round cap stopped the call with particles left");
             return SG_ERR_ROUND_LIMIT;
@@ -574,6 +583,10 @@ extern "C" sg_status sg_tracer_check(sg_tracer *t, int32_t *rounds, void *stream
     SG_CUDA(cudaMemcpyAsync(&c, t->ctrl, sizeof c, cudaMemcpyDeviceToHost, s));
     SG_CUDA(cudaStreamSynchronize(s));
     if (rounds) *rounds = (int32_t)c.last_rounds;
+    if (c.err & CTRL_ERR_TIMEOUT) {
+        set_error("a record copy of the advection kernel did not complete in time");
+        return SG_ERR_TIMEOUT;
+    }
     if (c.err & CTRL_ERR_ROUND_LIMIT) {
         set_error("the round cap stopped the trace with particles left");
         return SG_ERR_ROUND_LIMIT;

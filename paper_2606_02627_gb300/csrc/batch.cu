@@ -146,9 +146,9 @@ __global__ void __launch_bounds__(256) batch_round_kernel(const __grid_constant_
                     ++step;
                     ++here;
                     float *o = vslab + 3ll * step;
-                    o[0] = fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]);
-                    o[1] = fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]);
-                    o[2] = fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]);
+                    st_na(o, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
+                    st_na(o + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
+                    st_na(o + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
                     if (step >= max_steps) {
                         ev = EV_STOP;
                         st = SG_LINE_MAXSTEPS;

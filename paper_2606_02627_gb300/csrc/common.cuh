@@ -134,7 +134,7 @@ struct Ctrl {
     uint32_t pad[7];
 };
 
-enum { CTRL_ERR_ROUND_LIMIT = 1u };
+enum { CTRL_ERR_ROUND_LIMIT = 1u, CTRL_ERR_TIMEOUT = 2u };
 
 // ------------------------------------------------------------------ sampling helpers
 
@@ -268,18 +268,84 @@ __device__ __forceinline__ float3 lerp8(const float3 &c000, const float3 &c100, 
     return r;
 }
 
-// Eight corner samples of one cell record (CELL8 layout): 4 x 16-byte loads
-// for 8-byte samples, 8 x 16-byte loads for FP32.
+// Not finite in any component (NaN or inf).  The sum of magnitudes is finite
+// exactly when every component is finite, for |v| well below FLT_MAX.
+__device__ __forceinline__ bool bad3(float3 v) { return !(fabsf(v.x) + fabsf(v.y) + fabsf(v.z) < INFINITY); }
+
+// One 32-byte load through the read-only path (sm_100 and later): two
+// 16-byte halves.  p must be 32-byte aligned.
+__device__ __forceinline__ void ld_nc32(const void *p, uint4 &a, uint4 &b)
+{
+    asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+        : "l"(p));
+}
+
+// Asynchronous copies into shared memory and their completion on an
+// mbarrier (sm_80 and later).  Addresses are shared-window byte offsets.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// 16 bytes global -> shared through L1 (.ca: the line stays in L1).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// The barrier's pending arrival completes when every earlier cp.async of this
+// thread has landed (the barrier expects one arrival per phase).
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Non-blocking: has the phase of the given parity completed?
+__device__ __forceinline__ bool mbar_done(uint32_t bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// A cell record (CELL8 layout) as 16-byte chunks: 4 for 8-byte samples, 8 for
+// FP32 (float4 samples).
 template <int DT>
-__device__ __forceinline__ float3 trilerp_record(const typename Elem<DT>::T *__restrict__ rec, float fx, float fy,
-                                                 float fz)
+struct Record {
+    static constexpr int chunks = (DT == SG_F32) ? 8 : 4;
+    uint4 r[chunks];
+};
+
+// Reads one record: 32-byte loads (records are 64-byte aligned).
+template <int DT>
+__device__ __forceinline__ void load_record(const typename Elem<DT>::T *__restrict__ rec, Record<DT> &R)
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(rec);
+#pragma unroll
+    for (int k = 0; k < Record<DT>::chunks; k += 2) ld_nc32(p + k, R.r[k], R.r[k + 1]);
+}
+
+// Trilinear interpolation of the eight corners of a record.  bad reports a
+// sample that is not finite: for FX21 from the stored flags of the eight
+// corners (the interpolated value itself stays finite), for the float formats
+// from the interpolated value.
+template <int DT>
+__device__ __forceinline__ float3 interp_record(const Record<DT> &R, float fx, float fy, float fz, bool &bad)
 {
     if constexpr (DT == SG_FX21) {
         // x pairs interpolate the biased floats 2^23 + u directly: their
         // difference is exact, and the bias leaves with the lower corner
         // (the same value as subtracting it from both corners first)
-        const uint4 *r = reinterpret_cast<const uint4 *>(rec);
-        const uint4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
+        const uint4 a = R.r[0], b = R.r[1], c = R.r[2], d = R.r[3];
         const float C = 9437184.0f;
         auto raw = [](unsigned lo, unsigned hi) {
             return make_float3(__int_as_float(0x4B000000u | (lo & FX21_MASK)),
@@ -297,34 +363,48 @@ __device__ __forceinline__ float3 trilerp_record(const typename Elem<DT>::T *__r
         v.x = lerpf(lerpf(x00.x, x10.x, fy), lerpf(x01.x, x11.x, fy), fz);
         v.y = lerpf(lerpf(x00.y, x10.y, fy), lerpf(x01.y, x11.y, fy), fz);
         v.z = lerpf(lerpf(x00.z, x10.z, fy), lerpf(x01.z, x11.z, fy), fz);
-        if ((a.y | a.w | b.y | b.w | c.y | c.w | d.y | d.w) & FX21_FLAG) v = make_float3(NAN, NAN, NAN);
+        bad = ((a.y | a.w | b.y | b.w | c.y | c.w | d.y | d.w) & FX21_FLAG) != 0u;
         return v;
     } else if constexpr (DT == SG_F32) {
-        const float4 *r = reinterpret_cast<const float4 *>(rec);
-        const float4 a0 = __ldg(r), a1 = __ldg(r + 1), a2 = __ldg(r + 2), a3 = __ldg(r + 3);
-        const float4 a4 = __ldg(r + 4), a5 = __ldg(r + 5), a6 = __ldg(r + 6), a7 = __ldg(r + 7);
-        return lerp8(decode_elem<DT>(a0), decode_elem<DT>(a1), decode_elem<DT>(a2), decode_elem<DT>(a3),
-                     decode_elem<DT>(a4), decode_elem<DT>(a5), decode_elem<DT>(a6), decode_elem<DT>(a7), fx, fy, fz);
+        auto f4 = [](uint4 x) { return make_float4(__uint_as_float(x.x), __uint_as_float(x.y), __uint_as_float(x.z),
+                                                   __uint_as_float(x.w)); };
+        const float3 v = lerp8(decode_elem<DT>(f4(R.r[0])), decode_elem<DT>(f4(R.r[1])), decode_elem<DT>(f4(R.r[2])),
+                               decode_elem<DT>(f4(R.r[3])), decode_elem<DT>(f4(R.r[4])), decode_elem<DT>(f4(R.r[5])),
+                               decode_elem<DT>(f4(R.r[6])), decode_elem<DT>(f4(R.r[7])), fx, fy, fz);
+        bad = bad3(v);
+        return v;
     } else {
-        const uint4 *r = reinterpret_cast<const uint4 *>(rec);
-        const uint4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2), d = __ldg(r + 3);
-        return lerp8(decode_elem<DT>(make_uint2(a.x, a.y)), decode_elem<DT>(make_uint2(a.z, a.w)),
-                     decode_elem<DT>(make_uint2(b.x, b.y)), decode_elem<DT>(make_uint2(b.z, b.w)),
-                     decode_elem<DT>(make_uint2(c.x, c.y)), decode_elem<DT>(make_uint2(c.z, c.w)),
-                     decode_elem<DT>(make_uint2(d.x, d.y)), decode_elem<DT>(make_uint2(d.z, d.w)), fx, fy, fz);
+        const uint4 a = R.r[0], b = R.r[1], c = R.r[2], d = R.r[3];
+        const float3 v =
+            lerp8(decode_elem<DT>(make_uint2(a.x, a.y)), decode_elem<DT>(make_uint2(a.z, a.w)),
+                  decode_elem<DT>(make_uint2(b.x, b.y)), decode_elem<DT>(make_uint2(b.z, b.w)),
+                  decode_elem<DT>(make_uint2(c.x, c.y)), decode_elem<DT>(make_uint2(c.z, c.w)),
+                  decode_elem<DT>(make_uint2(d.x, d.y)), decode_elem<DT>(make_uint2(d.z, d.w)), fx, fy, fz);
+        bad = bad3(v);
+        return v;
     }
+}
+
+template <int DT>
+__device__ __forceinline__ float3 trilerp_record(const typename Elem<DT>::T *__restrict__ rec, float fx, float fy,
+                                                 float fz, bool &bad)
+{
+    Record<DT> R;
+    load_record<DT>(rec, R);
+    return interp_record<DT>(R, fx, fy, fz, bad);
 }
 
 // Trilinear interpolation inside one brick: (sx, sy, sz) is the storage index
 // of the lower corner (for CELL8: the cell index), (fx, fy, fz) the fractions.
-// Returns the value before the brick scale (multiply by it for world units).
+// Returns the value before the brick scale (multiply by it for world units);
+// bad as for trilerp_record.
 template <int DT, int LAYOUT>
 __device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict__ brick, const DevField &F,
-                                          int sx, int sy, int sz, float fx, float fy, float fz)
+                                          int sx, int sy, int sz, float fx, float fy, float fz, bool &bad)
 {
     if constexpr (LAYOUT == SG_LAYOUT_CELL8) {
         const int cell = (sz * F.C[1] + sy) * F.C[0] + sx;
-        return trilerp_record<DT>(brick + (long long)cell * 8, fx, fy, fz);
+        return trilerp_record<DT>(brick + (long long)cell * 8, fx, fy, fz, bad);
     } else {
         using O = Offsets<LAYOUT>;
         const int x0 = O::ox(sx, F), x1 = O::ox(sx + 1, F);
@@ -338,21 +418,31 @@ __device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict
         const auto e101 = load_elem<DT>(brick + (z1 + y0 + x1));
         const auto e011 = load_elem<DT>(brick + (z1 + y1 + x0));
         const auto e111 = load_elem<DT>(brick + (z1 + y1 + x1));
-        float3 v = lerp8(decode_elem<DT>(e000), decode_elem<DT>(e100), decode_elem<DT>(e010), decode_elem<DT>(e110),
-                         decode_elem<DT>(e001), decode_elem<DT>(e101), decode_elem<DT>(e011), decode_elem<DT>(e111), fx,
-                         fy, fz);
+        const float3 v =
+            lerp8(decode_elem<DT>(e000), decode_elem<DT>(e100), decode_elem<DT>(e010), decode_elem<DT>(e110),
+                  decode_elem<DT>(e001), decode_elem<DT>(e101), decode_elem<DT>(e011), decode_elem<DT>(e111), fx, fy,
+                  fz);
         if constexpr (DT == SG_FX21) {
-            if ((elem_flag<DT>(e000) | elem_flag<DT>(e100) | elem_flag<DT>(e010) | elem_flag<DT>(e110) |
-                 elem_flag<DT>(e001) | elem_flag<DT>(e101) | elem_flag<DT>(e011) | elem_flag<DT>(e111)))
-                v = make_float3(NAN, NAN, NAN);
+            bad = (elem_flag<DT>(e000) | elem_flag<DT>(e100) | elem_flag<DT>(e010) | elem_flag<DT>(e110) |
+                   elem_flag<DT>(e001) | elem_flag<DT>(e101) | elem_flag<DT>(e011) | elem_flag<DT>(e111)) != 0u;
+        } else {
+            bad = bad3(v);
         }
         return v;
     }
 }
 
-// Not finite in any component (NaN or inf).  The sum of magnitudes is finite
-// exactly when every component is finite, for |v| well below FLT_MAX.
-__device__ __forceinline__ bool bad3(float3 v) { return !(fabsf(v.x) + fabsf(v.y) + fabsf(v.z) < INFINITY); }
+// The same with a non-finite sample reported as a NaN value (every format).
+template <int DT, int LAYOUT>
+__device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict__ brick, const DevField &F,
+                                          int sx, int sy, int sz, float fx, float fy, float fz)
+{
+    bool bad;
+    float3 v = trilerp<DT, LAYOUT>(brick, F, sx, sy, sz, fx, fy, fz, bad);
+    if (DT == SG_FX21 && bad) v = make_float3(NAN, NAN, NAN);
+    return v;
+}
+
 
 // Stage point relative to a particle's cell: q = frac + dk gives the cell
 // offset floor(q) and the new fraction q - floor(q) (exact for |q| < 2^23);

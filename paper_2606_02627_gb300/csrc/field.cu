@@ -180,38 +180,41 @@ __global__ void brick_store_kernel(StoreArgs A, int layout)
     }
 }
 
-// CELL8: one thread per cell record; the eight corners are encoded in
-// registers and written as one contiguous 64- or 128-byte record.
+// CELL8: one thread per 16-byte chunk of a cell record (one FP32 corner, or
+// an x pair of 8-byte corners), so that the lanes of a warp write whole
+// records side by side: coalesced 512-byte stores.  Corner k of a record is
+// (x, y, z) = (k & 1, k >> 1 & 1, k >> 2) from the cell's lower corner.
 template <int DT>
 __global__ void brick_store_cell8_kernel(StoreArgs A)
 {
     using T = typename Elem<DT>::T;
+    constexpr int CPR = (DT == SG_F32) ? 8 : 4;    // chunks per record
+    constexpr int KPC = 8 / CPR;                    // corners per chunk
     const DevField &F = A.F;
     const int b = A.brick0 + blockIdx.y;
     const int bx = b % F.B[0], by = (b / F.B[0]) % F.B[1], bz = b / (F.B[0] * F.B[1]);
-    T *brick = reinterpret_cast<T *>(A.data + (long long)b * A.brick_bytes);
+    uint4 *brick = reinterpret_cast<uint4 *>(A.data + (long long)b * A.brick_bytes);
     const float s = (DT == SG_F32) ? 1.0f : A.scales[b];
-    const int cells = F.C[0] * F.C[1] * F.C[2];
-    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < cells; cell += gridDim.x * blockDim.x) {
+    const long long chunks = (long long)F.C[0] * F.C[1] * F.C[2] * CPR;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < chunks;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cell = (int)(i / CPR), j = (int)(i % CPR);
         const int cx = cell % F.C[0];
         const int t = cell / F.C[0];
         const int cy = t % F.C[1];
         const int cz = t / F.C[1];
-        T e[8];
+        T e[KPC];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int m = 0; m < KPC; ++m) {
+            const int k = j * KPC + m;
             const float *src = src_at(A, bx, by, bz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
-            e[k] = encode_elem<DT>(src[0], src[1], src[2], s);
+            e[m] = encode_elem<DT>(src[0], src[1], src[2], s);
         }
-        T *rec = brick + (long long)cell * 8;
-        if constexpr (DT == SG_F32) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) reinterpret_cast<float4 *>(rec)[k] = e[k];
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                reinterpret_cast<uint4 *>(rec)[k] = make_uint4(e[2 * k].x, e[2 * k].y, e[2 * k + 1].x, e[2 * k + 1].y);
-        }
+        uint4 out;
+        if constexpr (DT == SG_F32) out = make_uint4(__float_as_uint(e[0].x), __float_as_uint(e[0].y),
+                                                     __float_as_uint(e[0].z), __float_as_uint(e[0].w));
+        else out = make_uint4(e[0].x, e[0].y, e[1].x, e[1].y);
+        brick[i] = out;
     }
 }
 
@@ -290,7 +293,7 @@ sg_status launch_brick_store(sg_field *f, int slot, const float *src, int src_mo
     const int b0 = src_mode == 1 ? brick_index : 0;
     const int nbr = src_mode == 1 ? 1 : f->nb;
     A.brick0 = b0;
-    const long long total = d.layout == SG_LAYOUT_CELL8 ? (long long)A.F.C[0] * A.F.C[1] * A.F.C[2]
+    const long long total = d.layout == SG_LAYOUT_CELL8 ? (long long)A.F.C[0] * A.F.C[1] * A.F.C[2] * 4
                                                         : (long long)A.F.S[0] * A.F.S[1] * A.F.S[2];
     const int block = 256;
     dim3 grid(grid_x_for(total, block, nbr, f->ctx->sm_count), nbr);

@@ -33,23 +33,31 @@ __device__ __forceinline__ void brick_of(const DevField &F, const int c[3], Bric
     br.scale = (DT == SG_F32) ? 1.0f : __ldg(F.scales + id);
 }
 
-// Trilinear sample at global cell c, fraction f, from the particle's brick.
-// Returns SG_LINE_HALO if the point is outside the brick's ghost shell.
+// Trilinear sample at global cell c, fraction f, from the particle's brick,
+// before the brick scale.  Returns SG_LINE_HALO if the point is outside the
+// brick's ghost shell and SG_LINE_NANFIELD if the sample is not finite.
 template <int DT, int LAYOUT>
 __device__ __forceinline__ int sample_brick(const DevField &F, const BrickRef<DT> &br, const int c[3], const float f[3],
-                                            float3 &v)
+                                            float3 &u)
 {
     const int sx = c[0] - br.lo[0] + 1, sy = c[1] - br.lo[1] + 1, sz = c[2] - br.lo[2] + 1;
     if ((unsigned)sx > (unsigned)(F.S[0] - 2) || (unsigned)sy > (unsigned)(F.S[1] - 2) ||
         (unsigned)sz > (unsigned)(F.S[2] - 2))
         return SG_LINE_HALO;
-    v = trilerp<DT, LAYOUT>(br.data, F, sx, sy, sz, f[0], f[1], f[2]);
-    if (DT != SG_F32) {
-        v.x = __fmul_rn(v.x, br.scale);
-        v.y = __fmul_rn(v.y, br.scale);
-        v.z = __fmul_rn(v.z, br.scale);
-    }
-    return 0;
+    bool bad;
+    u = trilerp<DT, LAYOUT>(br.data, F, sx, sy, sz, f[0], f[1], f[2], bad);
+    return bad ? SG_LINE_NANFIELD : 0;
+}
+
+// The same at a cell the brick owns, which is always inside its ghost shell.
+template <int DT, int LAYOUT>
+__device__ __forceinline__ int sample_owned(const DevField &F, const BrickRef<DT> &br, const int c[3], const float f[3],
+                                            float3 &u)
+{
+    bool bad;
+    u = trilerp<DT, LAYOUT>(br.data, F, c[0] - br.lo[0] + 1, c[1] - br.lo[1] + 1, c[2] - br.lo[2] + 1, f[0], f[1], f[2],
+                            bad);
+    return bad ? SG_LINE_NANFIELD : 0;
 }
 
 __device__ __forceinline__ bool in_domain(const DevField &F, const int q[3], const float g[3])
@@ -67,6 +75,11 @@ __device__ __forceinline__ float out_dist(const DevField &F, const int q[3], con
 // inlines this step (tracer, Listing-1 form, request batch) then produces the
 // same bits for the same particle.
 //
+// The brick scale s of the compact formats is a power of two, so it moves
+// from the samples into the step factor without changing a bit:
+// (u s) (dt/h) = u (s dt/h) and |u s| = |u| s exactly (no overflow or
+// underflow at the scales a brick can have).
+//
 // One RK4 step of a particle owned by brick br.  On success updates (c, f)
 // and returns SG_LINE_ACTIVE; otherwise returns the stop status and leaves the
 // particle at P0.  margin is set for EXIT and STAGNANT.
@@ -74,15 +87,18 @@ template <int DT, int LAYOUT>
 __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3], float eps, const BrickRef<DT> &br,
                                            int c[3], float f[3], float &margin)
 {
+    float ds[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ds[a] = (DT == SG_F32) ? dtc[a] : __fmul_rn(dtc[a], br.scale);
     float3 v;
-    sample_brick<DT, LAYOUT>(F, br, c, f, v);            // P0 is owned: always inside the shell
-    if (bad3(v)) return SG_LINE_NANFIELD;
-    const float sp = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
+    if (sample_owned<DT, LAYOUT>(F, br, c, f, v)) return SG_LINE_NANFIELD;
+    float sp = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
+    if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
     if (sp < eps) {
         margin = (eps - sp) / eps;
         return SG_LINE_STAGNANT;
     }
-    float k1[3] = {__fmul_rn(v.x, dtc[0]), __fmul_rn(v.y, dtc[1]), __fmul_rn(v.z, dtc[2])};
+    float k1[3] = {__fmul_rn(v.x, ds[0]), __fmul_rn(v.y, ds[1]), __fmul_rn(v.z, ds[2])};
     int q[3];
     float g[3];
 #pragma unroll
@@ -92,8 +108,7 @@ __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3]
         return SG_LINE_EXIT;
     }
     if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
-    if (bad3(v)) return SG_LINE_NANFIELD;
-    float k2[3] = {__fmul_rn(v.x, dtc[0]), __fmul_rn(v.y, dtc[1]), __fmul_rn(v.z, dtc[2])};
+    float k2[3] = {__fmul_rn(v.x, ds[0]), __fmul_rn(v.y, ds[1]), __fmul_rn(v.z, ds[2])};
 #pragma unroll
     for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k2[a], c[a], q[a], g[a]);
     if (!in_domain(F, q, g)) {
@@ -101,8 +116,7 @@ __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3]
         return SG_LINE_EXIT;
     }
     if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
-    if (bad3(v)) return SG_LINE_NANFIELD;
-    float k3[3] = {__fmul_rn(v.x, dtc[0]), __fmul_rn(v.y, dtc[1]), __fmul_rn(v.z, dtc[2])};
+    float k3[3] = {__fmul_rn(v.x, ds[0]), __fmul_rn(v.y, ds[1]), __fmul_rn(v.z, ds[2])};
 #pragma unroll
     for (int a = 0; a < 3; ++a) locate(f[a], k3[a], c[a], q[a], g[a]);
     if (!in_domain(F, q, g)) {
@@ -110,8 +124,7 @@ __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3]
         return SG_LINE_EXIT;
     }
     if (int r = sample_brick<DT, LAYOUT>(F, br, q, g, v)) return r;
-    if (bad3(v)) return SG_LINE_NANFIELD;
-    const float k4[3] = {__fmul_rn(v.x, dtc[0]), __fmul_rn(v.y, dtc[1]), __fmul_rn(v.z, dtc[2])};
+    const float k4[3] = {__fmul_rn(v.x, ds[0]), __fmul_rn(v.y, ds[1]), __fmul_rn(v.z, ds[2])};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float d = __fmul_rn(__fadd_rn(__fadd_rn(k1[a], k4[a]), __fmul_rn(2.0f, __fadd_rn(k2[a], k3[a]))),
@@ -130,27 +143,48 @@ __device__ __forceinline__ int rk4_bricked(const DevField &F, const float dtc[3]
     return SG_LINE_ACTIVE;
 }
 
+// Stores and loads of data that no lane of this SM reads again soon (line
+// vertices, queue records) skip L1 allocation, which leaves L1 to the field's
+// cell records.
+__device__ __forceinline__ void st_na(float *p, float v)
+{
+    asm volatile("st.global.L1::no_allocate.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
+
+__device__ __forceinline__ void st_na4(void *p, uint4 v)
+{
+    asm volatile("st.global.L1::no_allocate.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w));
+}
+
+__device__ __forceinline__ uint4 ld_na4(const void *p)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ void store_particle(Particle *dst, const int c[3], const float f[3], uint32_t line,
                                                uint32_t step)
 {
-    float4 a = make_float4(f[0], f[1], f[2], __uint_as_float(line));
-    int4 b = make_int4(c[0], c[1], c[2], (int)step);
-    reinterpret_cast<float4 *>(dst)[0] = a;
-    reinterpret_cast<int4 *>(dst)[1] = b;
+    st_na4(dst, make_uint4(__float_as_uint(f[0]), __float_as_uint(f[1]), __float_as_uint(f[2]), line));
+    st_na4(reinterpret_cast<uint4 *>(dst) + 1, make_uint4((unsigned)c[0], (unsigned)c[1], (unsigned)c[2], step));
 }
 
 __device__ __forceinline__ void load_particle(const Particle *src, int c[3], float f[3], uint32_t &line, uint32_t &step)
 {
-    const float4 a = reinterpret_cast<const float4 *>(src)[0];
-    const int4 b = reinterpret_cast<const int4 *>(src)[1];
-    f[0] = a.x;
-    f[1] = a.y;
-    f[2] = a.z;
-    line = __float_as_uint(a.w);
-    c[0] = b.x;
-    c[1] = b.y;
-    c[2] = b.z;
-    step = (uint32_t)b.w;
+    const uint4 a = ld_na4(src);
+    const uint4 b = ld_na4(reinterpret_cast<const uint4 *>(src) + 1);
+    f[0] = __uint_as_float(a.x);
+    f[1] = __uint_as_float(a.y);
+    f[2] = __uint_as_float(a.z);
+    line = a.w;
+    c[0] = (int)b.x;
+    c[1] = (int)b.y;
+    c[2] = (int)b.z;
+    step = b.w;
 }
 
 // Warp-aggregated append: every lane of the warp calls it; lanes with `want`

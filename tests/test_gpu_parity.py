@@ -162,6 +162,26 @@ def test_bricked_equals_single_brick_bit_exact(ctx, dtype, layout):
             assert torch.equal(o.vertices, out[0].vertices)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16", "fx21"])
+def test_decoupled_lanes_equal_lockstep_bit_exact(ctx, dtype):
+    # CELL8 fields: the persistent kernel runs each lane's stages on its own
+    # record copies; the lockstep kernel loads every sample with the whole
+    # warp.  Same arithmetic, so the same bits, under any schedule.
+    g = inputs.cube_grid(57)
+    F = inputs.turbulence_field(g, inputs.turbulence_modes(11, n_modes=64, kmax=3)).numpy()
+    seeds = inputs.uniform_seeds(g, 4000, 11)
+    dt = 0.5 / oracle.max_speed(F, g.spacing)
+    for bricks, sched in [((4, 4, 4), dict(steps_per_round=13)), ((3, 5, 2), dict()),
+                          ((1, 1, 1), dict(steps_per_round=7, drain_steps=3, block_size=64, blocks_per_sm=3))]:
+        fld = make_field(ctx, g, F, bricks=bricks, dtype=dtype, layout="cell8")
+        _, a = run(ctx, fld, seeds, dt, 600, kernel="persistent", **sched)
+        _, b = run(ctx, fld, seeds, dt, 600, kernel="lockstep", **sched)
+        assert torch.equal(a.offsets, b.offsets)
+        assert torch.equal(a.vertices, b.vertices)
+        assert torch.equal(a.status, b.status)
+        assert torch.equal(a.margin, b.margin)
+
+
 def test_uneven_bricks_match_undecomposed(ctx):
     g = inputs.Grid((23, 17, 30), (0.5, -1.0, 2.0), (0.25, 0.5, 0.125))
     F = inputs.turbulence_field(g, inputs.turbulence_modes(5, n_modes=48, kmax=4)).numpy()
@@ -237,10 +257,11 @@ def test_turbulence_quantized(ctx, turb64, dtype, layout):
 
 # ---------------------------------------------------------------- step() and edge cases
 
-def test_step_calls_equal_one_trace(ctx, turb64):
+@pytest.mark.parametrize("layout", ["linear", "cell8"])
+def test_step_calls_equal_one_trace(ctx, turb64, layout):
     from paper_2606_02627_gb300 import api
     g, F, seeds, dt, ref = turb64
-    fld = make_field(ctx, g, F, bricks=(3, 2, 2))
+    fld = make_field(ctx, g, F, bricks=(3, 2, 2), layout=layout)
     tr = api.Tracer(ctx, fld, capacity=len(seeds), dt=dt, max_steps=300)
     tr.upload_seeds(torch.from_numpy(seeds).cuda())
     steps = 0
@@ -284,7 +305,8 @@ def test_edge_cases(ctx):
                       [4.0, 4.0, 4.0]], dtype=np.float32)
     ref = oracle.trace_streamlines(F, g.origin, g.spacing, seeds, 1.0, 12, eps=1e-6)
     for kernel, layout, bricks in [("persistent", "linear", (2, 2, 2)), ("per_step", "linear", (2, 1, 3)),
-                                   ("per_seed", "global", (1, 1, 1))]:
+                                   ("per_seed", "global", (1, 1, 1)), ("persistent", "cell8", (2, 2, 2)),
+                                   ("lockstep", "cell8", (2, 1, 3))]:
         fld = make_field(ctx, g, F, bricks=bricks, layout=layout)
         for ms in (0, 1, 12):
             r = ref if ms == 12 else oracle.trace_streamlines(F, g.origin, g.spacing, seeds, 1.0, ms, eps=1e-6)
