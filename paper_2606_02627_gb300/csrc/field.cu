@@ -7,6 +7,7 @@
 // one GPU every macrocell is a brick of the same device buffer; the halo is
 // the one-cell ghost shell that lets a particle owned by the brick finish a
 // step of at most one cell without touching another brick.
+#include <algorithm>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -180,10 +181,12 @@ __global__ void brick_store_kernel(StoreArgs A, int layout)
     }
 }
 
-// CELL8: one thread per 16-byte chunk of a cell record (one FP32 corner, or
-// an x pair of 8-byte corners), so that the lanes of a warp write whole
-// records side by side: coalesced 512-byte stores.  Corner k of a record is
-// (x, y, z) = (k & 1, k >> 1 & 1, k >> 2) from the cell's lower corner.
+// CELL8: one block per row of cell records (fixed y and z, all x), one thread
+// per 16-byte chunk of a record (one FP32 corner, or an x pair of 8-byte
+// corners), so that the lanes of a warp write whole records side by side
+// (coalesced 512-byte stores) and the row's index arithmetic is done once.
+// Corner k of a record is (x, y, z) = (k & 1, k >> 1 & 1, k >> 2) from the
+// cell's lower corner.
 template <int DT>
 __global__ void brick_store_cell8_kernel(StoreArgs A)
 {
@@ -195,26 +198,36 @@ __global__ void brick_store_cell8_kernel(StoreArgs A)
     const int bx = b % F.B[0], by = (b / F.B[0]) % F.B[1], bz = b / (F.B[0] * F.B[1]);
     uint4 *brick = reinterpret_cast<uint4 *>(A.data + (long long)b * A.brick_bytes);
     const float s = (DT == SG_F32) ? 1.0f : A.scales[b];
-    const long long chunks = (long long)F.C[0] * F.C[1] * F.C[2] * CPR;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < chunks;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int cell = (int)(i / CPR), j = (int)(i % CPR);
-        const int cx = cell % F.C[0];
-        const int t = cell / F.C[0];
-        const int cy = t % F.C[1];
-        const int cz = t / F.C[1];
-        T e[KPC];
+    const int rows = F.C[1] * F.C[2];
+    const int row_chunks = F.C[0] * CPR;
+    const int x0 = bx * F.n[0] - 1;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int cy = r % F.C[1], cz = r / F.C[1];
+        uint4 *dst = brick + (long long)r * row_chunks;
+        for (int j = threadIdx.x; j < row_chunks; j += blockDim.x) {
+            const int cx = j / CPR, jc = j % CPR;
+            T e[KPC];
 #pragma unroll
-        for (int m = 0; m < KPC; ++m) {
-            const int k = j * KPC + m;
-            const float *src = src_at(A, bx, by, bz, cx + (k & 1), cy + ((k >> 1) & 1), cz + (k >> 2));
-            e[m] = encode_elem<DT>(src[0], src[1], src[2], s);
+            for (int m = 0; m < KPC; ++m) {
+                const int k = jc * KPC + m;
+                const float *src;
+                if (A.src_mode == 1) {
+                    src = A.src + 3 * (((long long)(cz + (k >> 2)) * F.S[1] + cy + ((k >> 1) & 1)) * F.S[0] + cx +
+                                       (k & 1));
+                } else {
+                    const int gx = clampi(x0 + cx + (k & 1), 0, F.nm1[0]);
+                    const int gy = clampi(by * F.n[1] - 1 + cy + ((k >> 1) & 1), 0, F.nm1[1]);
+                    const int gz = clampi(bz * F.n[2] - 1 + cz + (k >> 2), 0, F.nm1[2]);
+                    src = A.src + 3 * (((long long)gz * F.dims[1] + gy) * F.dims[0] + gx);
+                }
+                e[m] = encode_elem<DT>(src[0], src[1], src[2], s);
+            }
+            uint4 out;
+            if constexpr (DT == SG_F32) out = make_uint4(__float_as_uint(e[0].x), __float_as_uint(e[0].y),
+                                                         __float_as_uint(e[0].z), __float_as_uint(e[0].w));
+            else out = make_uint4(e[0].x, e[0].y, e[1].x, e[1].y);
+            dst[j] = out;
         }
-        uint4 out;
-        if constexpr (DT == SG_F32) out = make_uint4(__float_as_uint(e[0].x), __float_as_uint(e[0].y),
-                                                     __float_as_uint(e[0].z), __float_as_uint(e[0].w));
-        else out = make_uint4(e[0].x, e[0].y, e[1].x, e[1].y);
-        brick[i] = out;
     }
 }
 
@@ -305,8 +318,11 @@ sg_status launch_brick_store(sg_field *f, int slot, const float *src, int src_mo
     brick_scale_kernel<<<(nbr + 255) / 256, 256, 0, s>>>(f->maxbits, A.scales, b0, nbr,
                                                          d.dtype == SG_FX21 ? 1.0f / 1048576.0f : 1.0f);
     SG_CUDA(cudaGetLastError());
+    const int rows = A.F.C[1] * A.F.C[2];
+    dim3 grid_rows((unsigned)std::min<long long>(rows, std::max(1, f->ctx->sm_count * 16 / nbr)), nbr);
     const bool ok = with_dtype(d.dtype, [&](auto D) {
-        if (d.layout == SG_LAYOUT_CELL8) brick_store_cell8_kernel<decltype(D)::value><<<grid, block, 0, s>>>(A);
+        if (d.layout == SG_LAYOUT_CELL8)
+            brick_store_cell8_kernel<decltype(D)::value><<<grid_rows, block, 0, s>>>(A);
         else brick_store_kernel<decltype(D)::value><<<grid, block, 0, s>>>(A, d.layout);
     });
     SG_CHECK(ok, SG_ERR_UNSUPPORTED, "unsupported dtype %d", d.dtype);
