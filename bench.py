@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--per-step", action="store_true", help="also time the one-launch-per-step kernel")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
-    ap.add_argument("--schedule", default="", help="block,blocks_per_sm,steps_per_round")
+    ap.add_argument("--schedule", default="", help="block,blocks_per_sm,steps_per_round[,drain_steps]")
     ap.add_argument("--requests", type=int, default=160, help="serve: requests in the Poisson stream")
     ap.add_argument("--config", default="steady", choices=["steady", "streak", "serve"],
                     help="steady: brick-decomposed streamlines (the headline); streak: unsteady streaklines with "
@@ -413,8 +413,10 @@ def main():
     stream.synchronize()
     sched = {}
     if args.schedule:
-        b, bps, spr = (int(x) for x in args.schedule.split(","))
-        sched = dict(block_size=b, blocks_per_sm=bps, steps_per_round=spr)
+        vals = [int(x) for x in args.schedule.split(",")]
+        sched = dict(block_size=vals[0], blocks_per_sm=vals[1], steps_per_round=vals[2])
+        if len(vals) > 3:
+            sched["drain_steps"] = vals[3]
 
     seeds_np = inputs.uniform_seeds(grid, args.seeds, rank_seed(1, rank))
     seeds_dev = torch.from_numpy(seeds_np).to(dev)

@@ -224,12 +224,15 @@ typedef struct {
     int32_t block_size;    /* threads per CTA (multiple of 32, <= 1024)              */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent grid                     */
     int32_t steps_per_round; /* steps a particle may take in one round before it is
-                                re-queued in its own brick                          */
+                                re-queued in its own brick (0 = default: 256 for the
+                                decoupled-lane kernel, 128 otherwise)               */
     int32_t max_rounds;    /* round cap of one trace / step call                     */
     int32_t drain_steps;   /* once a warp finds the round's queue empty, its lanes take
                               at most this many more steps before re-queueing their
-                              particles for the next round (0 = no limit): shortens
-                              the end of a round at the price of more rounds      */
+                              particles for the next round: shortens the end of a
+                              round at the price of more rounds.  0 = library
+                              default (128 for the decoupled-lane kernel, no limit
+                              otherwise); negative = no limit                      */
 } sg_tracer_params;
 
 /* Fills p with the defaults (streamline, persistent kernel, eps 1e-6,

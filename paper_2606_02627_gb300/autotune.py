@@ -1,8 +1,9 @@
 """Schedule autotuner of the persistent advection kernel.
 
 Tunables (all `sg_tracer_params` fields): threads per CTA, CTAs per SM of the
-persistent grid, and steps a particle may take per round before it is
-re-queued in its own brick.  The search is successive halving: every
+persistent grid, steps a particle may take per round before it is re-queued
+in its own brick, and whether a round's end is cut short once its queue is
+empty (the library's drain default, or no limit).  The search is successive halving: every
 candidate traces a small prefix of the seeds, the faster half traces a larger
 prefix, and so on; the winner is cached in a JSON file keyed by the GPU, the
 field's storage type / layout / size / bricks and the problem size, so a
@@ -27,13 +28,23 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "streamgb", "aut
 
 
 def candidates(max_threads_per_sm: int = 2048, regs_limit_threads: int = 1024):
-    """Grid of (block_size, blocks_per_sm, steps_per_round) to try."""
+    """Grid of (block_size, blocks_per_sm, steps_per_round, drain_steps) to try
+    (drain_steps 0: the library default; -1: no limit)."""
     out = []
-    for block, threads, spr in itertools.product((64, 128, 256), (256, 384, 512, 768, 1024), (32, 128, 512)):
+    for block, threads, spr, drain in itertools.product((64, 128, 256), (256, 384, 512, 768, 1024), (128, 256, 512),
+                                                         (0, -1)):
         if threads > min(max_threads_per_sm, regs_limit_threads) or threads % block:
             continue
-        out.append((block, threads // block, spr))
+        out.append((block, threads // block, spr, drain))
     return out
+
+
+def schedule_of(c) -> dict:
+    """The sg_tracer_params fields of one candidate tuple."""
+    sched = dict(block_size=c[0], blocks_per_sm=c[1], steps_per_round=c[2])
+    if len(c) > 3:
+        sched["drain_steps"] = c[3]
+    return sched
 
 
 def shape_key(field: api.Field, n_seeds: int, max_steps: int) -> str:
@@ -57,7 +68,7 @@ def _time_trace(tr: api.Tracer, seeds: torch.Tensor, stream) -> float:
 def tune(ctx: api.Context, field: api.Field, seeds: torch.Tensor, dt: float, max_steps: int,
          cands=None, first: int = 1 << 16, rounds: int = 3, cache: str | None = DEFAULT_CACHE,
          stream=None, log=None) -> dict:
-    """Returns the fastest {block_size, blocks_per_sm, steps_per_round} for this shape."""
+    """Returns the fastest {block_size, blocks_per_sm, steps_per_round, drain_steps} for this shape."""
     key = shape_key(field, int(seeds.shape[0]), max_steps)
     db = {}
     if cache and os.path.exists(cache):
@@ -76,7 +87,7 @@ def tune(ctx: api.Context, field: api.Field, seeds: torch.Tensor, dt: float, max
         prefix = seeds[:n].contiguous()
         scored = []
         for c in cands:
-            sched = dict(block_size=c[0], blocks_per_sm=c[1], steps_per_round=c[2])
+            sched = schedule_of(c)
             tr = api.Tracer(ctx, field, capacity=n, dt=dt, max_steps=max_steps, **sched)
             _time_trace(tr, prefix, stream)            # warm the graph
             ms = _time_trace(tr, prefix, stream)
@@ -91,8 +102,7 @@ def tune(ctx: api.Context, field: api.Field, seeds: torch.Tensor, dt: float, max
         if len(cands) == 1 or n >= seeds.shape[0]:
             break
         n = min(int(seeds.shape[0]), n * 4)
-    best = cands[0]
-    sched = dict(block_size=best[0], blocks_per_sm=best[1], steps_per_round=best[2])
+    sched = schedule_of(cands[0])
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         db[key] = {"schedule": sched, "history": history, "seconds": time.time() - t_start}

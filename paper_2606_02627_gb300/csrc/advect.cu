@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
     const uint32_t horizon = P.ctrl->horizon;
     bool active = false, pending = false;
     bool drained = q_count == 0;
-    uint32_t drain_left = P.drain_steps;
+    // four passes per step
+    uint32_t drain_left = P.drain_steps >= 0x20000000u ? 0xffffffffu : P.drain_steps * 4u;
     unsigned parity = 0, waited = 0;
     int c[3] = {0, 0, 0}, q[3] = {0, 0, 0};               // P0 and the current sample point
     float f[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};

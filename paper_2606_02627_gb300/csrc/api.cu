@@ -153,7 +153,6 @@ static sg_status check_params(const sg_field *f, const sg_tracer_params *p)
     SG_CHECK(p->blocks_per_sm >= 0 && p->blocks_per_sm <= 32, SG_ERR_INVALID_ARG, "blocks_per_sm in [0, 32]");
     SG_CHECK(p->steps_per_round >= 0, SG_ERR_INVALID_ARG, "steps_per_round must be >= 0");
     SG_CHECK(p->max_rounds >= 0, SG_ERR_INVALID_ARG, "max_rounds must be >= 0");
-    SG_CHECK(p->drain_steps >= 0, SG_ERR_INVALID_ARG, "drain_steps must be >= 0");
     if (p->mode == SG_STREAMLINE) {
         SG_CHECK(p->max_steps >= 0 && p->max_steps < (1 << 27), SG_ERR_INVALID_ARG, "max_steps out of range");
         SG_CHECK(p->kernel == SG_KERNEL_PERSISTENT || p->kernel == SG_KERNEL_PER_SEED ||
@@ -282,8 +281,6 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
     t->ws_bytes = bytes;
     t->nb = f->nb;
     tracer_layout(f, p, capacity, t, (char *)workspace);
-    if (t->p.steps_per_round <= 0) t->p.steps_per_round = 128;
-    if (t->p.drain_steps <= 0) t->p.drain_steps = 0x7fffffff;
     t->block = p->block_size > 0 ? p->block_size : 256;
     // default resident threads per SM (measured on GB300): 512 for the kernels
     // that read every sample through L1, where more particles per SM thrash the
@@ -292,6 +289,11 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
     // issue instead
     const bool decoupled = p->kernel == SG_KERNEL_PERSISTENT && f->desc.layout == SG_LAYOUT_CELL8;
     const int threads_per_sm = decoupled ? 768 : 512;
+    // round length (measured on GB300): the decoupled kernel gains from longer
+    // rounds whose ends are cut short once the queue is empty
+    if (t->p.steps_per_round <= 0) t->p.steps_per_round = decoupled ? 256 : 128;
+    if (t->p.drain_steps == 0) t->p.drain_steps = decoupled ? 128 : 0x7fffffff;
+    else if (t->p.drain_steps < 0) t->p.drain_steps = 0x7fffffff;
     const int per_sm = p->blocks_per_sm > 0 ? p->blocks_per_sm : (threads_per_sm + t->block - 1) / t->block;
     t->grid = ctx->sm_count * (per_sm > 0 ? per_sm : 1);
     if (t->p.mode == SG_STREAMLINE) {
