@@ -93,6 +93,13 @@ enum {
 
 enum { SG_STREAMLINE = 0, SG_STREAKLINE = 1 };
 
+/* Direction of streamline integration (the paper's Tracer advects forward
+ * only; backward lines follow -v, the same RK4 with -dt).  With
+ * SG_DIR_BOTH a tracer holds two lines per seed: line i forward and line
+ * n + i backward from seed i (n seeds uploaded); sg_tracer_get_joined joins
+ * them into one polyline through the seed. */
+enum { SG_DIR_FORWARD = 0, SG_DIR_BACKWARD = 1, SG_DIR_BOTH = 2 };
+
 /* Advection kernel of a streamline tracer. */
 enum {
     SG_KERNEL_PERSISTENT = 0,  /* bricked field; persistent warps refill lanes from
@@ -233,6 +240,7 @@ typedef struct {
                               round at the price of more rounds.  0 = library
                               default (128 for the decoupled-lane kernel, no limit
                               otherwise); negative = no limit                      */
+    int32_t direction;     /* SG_DIR_* (streamlines; 0 = forward)                   */
 } sg_tracer_params;
 
 /* Fills p with the defaults (streamline, persistent kernel, eps 1e-6,
@@ -305,9 +313,50 @@ sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t *n_vertice
                               float *vertices, uint8_t *status, float *margin, int32_t *line_source,
                               void *stream);
 
+/* Bidirectional readback (SG_DIR_BOTH): one polyline per seed, the backward
+ * line reversed (the seed not repeated) followed by the forward line, so that
+ * polyline i runs along the flow through seed i.  Two calls, as
+ * sg_tracer_get_lines: with offsets and vertices NULL it only returns n_lines
+ * (= seeds) and n_vertices (synchronising the stream); then with device
+ * buffers of n_lines+1 int64 offsets, 3*n_vertices floats and n_lines int64
+ * seed_vertex (nullable: the index of the seed within its polyline, -1 for
+ * an OUT seed).  Per-direction status and margin come from
+ * sg_tracer_get_lines (lines i and n + i).  SG_ERR_STATE unless the tracer
+ * was created with SG_DIR_BOTH; asynchronous when the buffers are given. */
+sg_status sg_tracer_get_joined(sg_tracer *t, int64_t *n_lines, int64_t *n_vertices, int64_t *offsets,
+                               float *vertices, int64_t *seed_vertex, void *stream);
+
 /* Successful RK4 steps of the current trace summed over all lines (the unit of
  * the particle-steps/s metric).  Synchronous. */
 sg_status sg_tracer_total_steps(sg_tracer *t, int64_t *steps, void *stream);
+
+/* ------------------------------------------------------- seed-shape kernels */
+
+/* Seed points from control shapes, generated on the device (the low-level
+ * interface's convenience kernels for seeds placed uniformly on lines and
+ * planes, Sec. 3.1).  World coordinates; positions are computed in double
+ * precision with explicit round-to-nearest operations and rounded once to
+ * float32.  out: device or page-locked host memory, 3 floats per point
+ * (x, y, z), caller-owned.  Asynchronous on stream; SG_ERR_INVALID_ARG on
+ * NULL vectors, negative counts or an unusable out pointer. */
+
+/* n points evenly spaced on the segment a..b, both ends included
+ * (point i at a + (b - a) i / (n - 1); n = 1 gives a). */
+sg_status sg_seeds_rake(const double a[3], const double b[3], int64_t n, float *out, void *stream);
+
+/* nu x nv points evenly spaced on the parallelogram origin + s u + t v,
+ * s, t in [0, 1] (s = i / (nu - 1), t = j / (nv - 1)); point (i, j) at index
+ * j nu + i. */
+sg_status sg_seeds_plane(const double origin[3], const double u[3], const double v[3], int64_t nu, int64_t nv,
+                         float *out, void *stream);
+
+/* n points uniform at random in the box [lo, hi] (per axis): coordinate c of
+ * point i is lo + (hi - lo) u with u the top 53 bits of value 3i + c of the
+ * counter-based SplitMix64 stream (seed, stream_id) (Steele, Lea, Flood
+ * 2014: value k = mix64(key + (k + 1) G), key = mix64(seed G +
+ * 0x632BE59BD9B4E019 (stream_id + 1)), G = 0x9E3779B97F4A7C15). */
+sg_status sg_seeds_box(const double lo[3], const double hi[3], int64_t n, uint64_t seed, uint64_t stream_id,
+                       float *out, void *stream);
 
 /* -------------------------------------------------------------- request batch */
 

@@ -29,6 +29,7 @@ SG_F32, SG_BF16, SG_F16, SG_FX21 = 0, 1, 2, 3
 SG_LAYOUT_LINEAR, SG_LAYOUT_TILED4, SG_LAYOUT_CELL8, SG_FIELD_GLOBAL = 0, 1, 2, 16
 SG_STREAMLINE, SG_STREAKLINE = 0, 1
 SG_KERNEL_PERSISTENT, SG_KERNEL_PER_SEED, SG_KERNEL_PER_STEP, SG_KERNEL_LOCKSTEP = 0, 1, 2, 3
+SG_DIR_FORWARD, SG_DIR_BACKWARD, SG_DIR_BOTH = 0, 1, 2
 SG_LINE_ACTIVE, SG_LINE_MAXSTEPS, SG_LINE_EXIT, SG_LINE_STAGNANT = 0, 1, 2, 3
 SG_LINE_NANFIELD, SG_LINE_OUT, SG_LINE_HALO, SG_LINE_TIE = 4, 5, 6, 0x80
 
@@ -44,7 +45,7 @@ class sg_tracer_params(ctypes.Structure):
                 ("max_steps", ctypes.c_int32), ("eps", ctypes.c_float), ("tie_cells", ctypes.c_float),
                 ("tie_eps_rel", ctypes.c_float), ("inject_steps", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("steps_per_round", ctypes.c_int32),
-                ("max_rounds", ctypes.c_int32), ("drain_steps", ctypes.c_int32)]
+                ("max_rounds", ctypes.c_int32), ("drain_steps", ctypes.c_int32), ("direction", ctypes.c_int32)]
 
 
 class sg_batch_desc(ctypes.Structure):
@@ -93,6 +94,10 @@ SIGNATURES = {
     "sg_tracer_trace_timed": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), P, P, i32, P], i32),
     "sg_tracer_get_lines": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P, P, P], i32),
     "sg_tracer_total_steps": ([P, ctypes.POINTER(i64), P], i32),
+    "sg_tracer_get_joined": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P], i32),
+    "sg_seeds_rake": ([P, P, i64, P, P], i32),
+    "sg_seeds_plane": ([P, P, P, i64, i64, P, P], i32),
+    "sg_seeds_box": ([P, P, i64, ctypes.c_uint64, ctypes.c_uint64, P, P], i32),
     "sg_lines_compact_static": ([P, i64, P, i64, P, P, P], i32),
     "sg_batch_required_bytes": ([P, ctypes.POINTER(sg_batch_desc), ctypes.POINTER(sz)], i32),
     "sg_batch_create": ([P, ctypes.POINTER(sg_batch_desc), P, sz, PP], i32),

@@ -19,6 +19,7 @@ LAYOUTS = {"linear": L.SG_LAYOUT_LINEAR, "tiled4": L.SG_LAYOUT_TILED4, "cell8": 
            "global": L.SG_FIELD_GLOBAL}
 KERNELS = {"persistent": L.SG_KERNEL_PERSISTENT, "per_seed": L.SG_KERNEL_PER_SEED, "per_step": L.SG_KERNEL_PER_STEP,
            "lockstep": L.SG_KERNEL_LOCKSTEP}
+DIRECTIONS = {"forward": L.SG_DIR_FORWARD, "backward": L.SG_DIR_BACKWARD, "both": L.SG_DIR_BOTH}
 STATUS_NAMES = {0: "ACTIVE", 1: "MAXSTEPS", 2: "EXIT", 3: "STAGNANT", 4: "NANFIELD", 5: "OUT", 6: "HALO"}
 
 
@@ -149,9 +150,48 @@ class Lines:
         return self.offsets[1:] - self.offsets[:-1]
 
 
+@dataclass
+class JoinedLines:
+    offsets: torch.Tensor      # int64 [n_seeds + 1]
+    vertices: torch.Tensor     # float32 [n_vertices, 3] world: backward part reversed, then forward
+    seed_vertex: torch.Tensor  # int64 [n_seeds]: index of the seed in its polyline (-1: OUT seed)
+
+    def lengths(self):
+        return self.offsets[1:] - self.offsets[:-1]
+
+
+def _vec3(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(3))
+
+
+def seeds_rake(a, b, n: int, device="cuda", stream=None) -> torch.Tensor:
+    """n seeds evenly spaced on the world segment a..b (device kernel)."""
+    out = torch.empty((max(int(n), 1), 3), dtype=torch.float32, device=device)
+    va, vb = _vec3(a), _vec3(b)
+    call("sg_seeds_rake", _ptr(va), _ptr(vb), int(n), _ptr(out), _stream(stream))
+    return out[:int(n)]
+
+
+def seeds_plane(origin, u, v, nu: int, nv: int, device="cuda", stream=None) -> torch.Tensor:
+    """nu x nv seeds evenly spaced on the parallelogram origin + s u + t v (device kernel)."""
+    n = int(nu) * int(nv)
+    out = torch.empty((max(n, 1), 3), dtype=torch.float32, device=device)
+    vo, vu, vv = _vec3(origin), _vec3(u), _vec3(v)
+    call("sg_seeds_plane", _ptr(vo), _ptr(vu), _ptr(vv), int(nu), int(nv), _ptr(out), _stream(stream))
+    return out[:n]
+
+
+def seeds_box(lo, hi, n: int, seed: int, stream_id: int = 0, device="cuda", stream=None) -> torch.Tensor:
+    """n seeds uniform at random in the world box [lo, hi] (SplitMix64 stream, device kernel)."""
+    out = torch.empty((max(int(n), 1), 3), dtype=torch.float32, device=device)
+    vl, vh = _vec3(lo), _vec3(hi)
+    call("sg_seeds_box", _ptr(vl), _ptr(vh), int(n), int(seed), int(stream_id), _ptr(out), _stream(stream))
+    return out[:int(n)]
+
+
 def tracer_params(dt, max_steps=1000, mode="streamline", kernel="persistent", eps=1e-6, tie_cells=1e-3,
                   tie_eps_rel=1e-3, inject_steps=1, block_size=0, blocks_per_sm=0, steps_per_round=0,
-                  max_rounds=0, drain_steps=0) -> L.sg_tracer_params:
+                  max_rounds=0, drain_steps=0, direction="forward") -> L.sg_tracer_params:
     p = L.sg_tracer_params()
     call("sg_tracer_params_default", ctypes.byref(p))
     p.mode = L.SG_STREAMLINE if mode == "streamline" else L.SG_STREAKLINE
@@ -167,6 +207,7 @@ def tracer_params(dt, max_steps=1000, mode="streamline", kernel="persistent", ep
     p.steps_per_round = int(steps_per_round)
     p.max_rounds = int(max_rounds)
     p.drain_steps = int(drain_steps)
+    p.direction = DIRECTIONS[direction] if isinstance(direction, str) else int(direction)
     return p
 
 
@@ -248,6 +289,18 @@ class Tracer:
         call("sg_tracer_get_lines", self.h, None, None, _ptr(off), _ptr(vert), _ptr(st), _ptr(mg), _ptr(src),
              _stream(stream))
         return Lines(off, vert[:nv], st[:nl], mg[:nl], src[:nl])
+
+    def get_joined(self, stream=None) -> JoinedLines:
+        """Bidirectional tracers: one polyline per seed through the seed (device)."""
+        nl = ctypes.c_int64()
+        nv = ctypes.c_int64()
+        call("sg_tracer_get_joined", self.h, ctypes.byref(nl), ctypes.byref(nv), None, None, None, _stream(stream))
+        dev = f"cuda:{self.ctx.device}"
+        off = torch.empty(nl.value + 1, dtype=torch.int64, device=dev)
+        vert = torch.empty((max(nv.value, 1), 3), dtype=torch.float32, device=dev)
+        sv = torch.empty(max(nl.value, 1), dtype=torch.int64, device=dev)
+        call("sg_tracer_get_joined", self.h, None, None, _ptr(off), _ptr(vert), _ptr(sv), _stream(stream))
+        return JoinedLines(off, vert[:nv.value], sv[:nl.value])
 
     def total_steps(self, stream=None) -> int:
         n = ctypes.c_int64()

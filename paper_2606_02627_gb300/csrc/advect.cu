@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256) round_kernel(const __grid_constant__ Line
     int c[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f};
     uint32_t line = 0, step = 0, here = 0;
+    float dtc[3] = {0.f, 0.f, 0.f};          // dt/h of this lane's line (negated backward)
     BrickRef<DT> br;
     br.data = nullptr;
     br.scale = 1.0f;
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(256) round_kernel(const __grid_constant__ Line
                 if (my < q_count) {
                     load_particle(P.q + my, c, f, line, step);
                     brick_of<DT>(P.F, c, br);
+                    line_dtc(P, line, dtc);
                     active = true;
                     here = 0;
                 }
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(256) round_kernel(const __grid_constant__ Line
             } else if (here >= P.steps_per_round) {
                 ev = EV_APPEND;
             } else {
-                st = rk4_bricked<DT, LAYOUT>(P.F, P.dtc, P.eps, br, c, f, margin);
+                st = rk4_bricked<DT, LAYOUT>(P.F, dtc, P.eps, br, c, f, margin);
                 if (st != SG_LINE_ACTIVE) {
                     ev = EV_STOP;
                 } else {
@@ -212,9 +214,11 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
                 if (my < q_count) {
                     load_particle(P.q + my, c, f, line, step);
                     brick_of<DT>(F, c, br);
+                    float dtc[3];
+                    line_dtc(P, line, dtc);
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
-                        ds[a] = (DT == SG_F32) ? P.dtc[a] : __fmul_rn(P.dtc[a], br.scale);
+                        ds[a] = (DT == SG_F32) ? dtc[a] : __fmul_rn(dtc[a], br.scale);
                         q[a] = c[a];
                         g[a] = f[a];
                     }
@@ -372,7 +376,9 @@ __global__ void __launch_bounds__(256) per_step_kernel(const __grid_constant__ L
             } else {
                 BrickRef<DT> br;
                 brick_of<DT>(P.F, c, br);
-                st = rk4_bricked<DT, LAYOUT>(P.F, P.dtc, P.eps, br, c, f, margin);
+                float dtc[3];
+                line_dtc(P, line, dtc);
+                st = rk4_bricked<DT, LAYOUT>(P.F, dtc, P.eps, br, c, f, margin);
                 if (st != SG_LINE_ACTIVE) {
                     ev = EV_STOP;
                 } else {
@@ -455,9 +461,12 @@ __global__ void __launch_bounds__(256) per_seed_kernel(const __grid_constant__ L
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n_lines;
          i += (long long)gridDim.x * blockDim.x) {
         // index-space seed, converted in double precision
-        const double sx = ((double)P.seeds[3 * i] - P.origin_d[0]) / P.spacing_d[0];
-        const double sy = ((double)P.seeds[3 * i + 1] - P.origin_d[1]) / P.spacing_d[1];
-        const double sz = ((double)P.seeds[3 * i + 2] - P.origin_d[2]) / P.spacing_d[2];
+        const float *sd = P.seeds + 3 * seed_of(P, i);
+        float dtc[3];
+        line_dtc(P, i, dtc);
+        const double sx = ((double)sd[0] - P.origin_d[0]) / P.spacing_d[0];
+        const double sy = ((double)sd[1] - P.origin_d[1]) / P.spacing_d[1];
+        const double sz = ((double)sd[2] - P.origin_d[2]) / P.spacing_d[2];
         if (!(sx >= 0.0 && sx <= F.nm1[0] && sy >= 0.0 && sy <= F.nm1[1] && sz >= 0.0 && sz <= F.nm1[2])) {
             P.line_len[i] = 0;
             P.line_status[i] = SG_LINE_OUT;
@@ -466,9 +475,9 @@ __global__ void __launch_bounds__(256) per_seed_kernel(const __grid_constant__ L
         }
         float px = (float)sx, py = (float)sy, pz = (float)sz;
         float *out = P.slab + (long long)i * P.W * 3;
-        out[0] = P.seeds[3 * i];
-        out[1] = P.seeds[3 * i + 1];
-        out[2] = P.seeds[3 * i + 2];
+        out[0] = sd[0];
+        out[1] = sd[1];
+        out[2] = sd[2];
         uint32_t step = 0;
         int st = SG_LINE_MAXSTEPS;
         float margin = INFINITY;
@@ -477,22 +486,22 @@ __global__ void __launch_bounds__(256) per_seed_kernel(const __grid_constant__ L
             if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
             const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
             if (sp < P.eps) { st = SG_LINE_STAGNANT; margin = (P.eps - sp) / P.eps; break; }
-            const float k1x = v.x * P.dtc[0], k1y = v.y * P.dtc[1], k1z = v.z * P.dtc[2];
+            const float k1x = v.x * dtc[0], k1y = v.y * dtc[1], k1z = v.z * dtc[2];
             float qx = px + 0.5f * k1x, qy = py + 0.5f * k1y, qz = pz + 0.5f * k1z;
             if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
             v = sample_global(Fg, F, qx, qy, qz);
             if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-            const float k2x = v.x * P.dtc[0], k2y = v.y * P.dtc[1], k2z = v.z * P.dtc[2];
+            const float k2x = v.x * dtc[0], k2y = v.y * dtc[1], k2z = v.z * dtc[2];
             qx = px + 0.5f * k2x; qy = py + 0.5f * k2y; qz = pz + 0.5f * k2z;
             if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
             v = sample_global(Fg, F, qx, qy, qz);
             if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-            const float k3x = v.x * P.dtc[0], k3y = v.y * P.dtc[1], k3z = v.z * P.dtc[2];
+            const float k3x = v.x * dtc[0], k3y = v.y * dtc[1], k3z = v.z * dtc[2];
             qx = px + k3x; qy = py + k3y; qz = pz + k3z;
             if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
             v = sample_global(Fg, F, qx, qy, qz);
             if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-            const float k4x = v.x * P.dtc[0], k4y = v.y * P.dtc[1], k4z = v.z * P.dtc[2];
+            const float k4x = v.x * dtc[0], k4y = v.y * dtc[1], k4z = v.z * dtc[2];
             qx = px + (k1x + k4x + 2.0f * (k2x + k3x)) * (1.0f / 6.0f);
             qy = py + (k1y + k4y + 2.0f * (k2y + k3y)) * (1.0f / 6.0f);
             qz = pz + (k1z + k4z + 2.0f * (k2z + k3z)) * (1.0f / 6.0f);
@@ -523,11 +532,12 @@ __global__ void upload_kernel(const __grid_constant__ LineParams P)
         int c[3] = {0, 0, 0};
         float f[3] = {0.f, 0.f, 0.f};
         if (i < n) {
+            const float *sd = P.seeds + 3 * seed_of(P, i);
             double p[3];
             bool inside = true;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                p[a] = ((double)P.seeds[3 * i + a] - P.origin_d[a]) / P.spacing_d[a];
+                p[a] = ((double)sd[a] - P.origin_d[a]) / P.spacing_d[a];
                 inside = inside && (p[a] >= 0.0 && p[a] <= (double)P.F.nm1[a]);
             }
             if (!inside) {
@@ -546,9 +556,9 @@ __global__ void upload_kernel(const __grid_constant__ LineParams P)
                     }
                 }
                 float *o = P.slab + (long long)i * P.W * 3;
-                o[0] = P.seeds[3 * i];
-                o[1] = P.seeds[3 * i + 1];
-                o[2] = P.seeds[3 * i + 2];
+                o[0] = sd[0];
+                o[1] = sd[1];
+                o[2] = sd[2];
                 P.line_len[i] = 1;
                 P.line_status[i] = SG_LINE_ACTIVE;
                 P.line_margin[i] = INFINITY;
@@ -565,7 +575,7 @@ sg_status launch_upload(sg_tracer *t, cudaStream_t s)
 {
     LineParams P = line_params(t);
     if (t->p.kernel == SG_KERNEL_PER_SEED) return SG_OK;   // the per-seed kernel reads the seeds itself
-    int grid = (int)((t->n_seeds + 255) / 256);
+    int grid = (int)((t->n_lines + 255) / 256);
     if (grid > t->ctx->sm_count * 16) grid = t->ctx->sm_count * 16;
     if (grid < 1) grid = 1;
     upload_kernel<<<grid, 256, 0, s>>>(P);
@@ -576,9 +586,9 @@ sg_status launch_upload(sg_tracer *t, cudaStream_t s)
 sg_status launch_per_seed(sg_tracer *t, cudaStream_t s)
 {
     LineParams P = line_params(t);
-    if (t->n_seeds == 0) return SG_OK;
+    if (t->n_lines == 0) return SG_OK;
     const int block = t->block;
-    long long grid = (t->n_seeds + block - 1) / block;
+    long long grid = (t->n_lines + block - 1) / block;
     if (grid > t->grid) grid = t->grid;
     per_seed_kernel<<<(unsigned)grid, block, 0, s>>>(P);
     SG_CUDA(cudaGetLastError());

@@ -60,7 +60,9 @@ LineParams line_params(const sg_tracer *t)
     P.line_status = t->line_status;
     P.line_margin = t->line_margin;
     P.W = (long long)t->p.max_steps + 1;
-    P.n_lines = t->n_seeds;
+    P.n_lines = t->n_lines;
+    P.n_seed = t->n_seeds;
+    P.n_fwd = t->p.direction == SG_DIR_FORWARD ? t->n_lines : (t->p.direction == SG_DIR_BACKWARD ? 0 : t->n_seeds);
     for (int a = 0; a < 3; ++a) {
         P.dtc[a] = (float)(t->p.dt / f->desc.spacing[a]);
         P.origin_d[a] = f->desc.origin[a];
@@ -153,6 +155,8 @@ static sg_status check_params(const sg_field *f, const sg_tracer_params *p)
     SG_CHECK(p->blocks_per_sm >= 0 && p->blocks_per_sm <= 32, SG_ERR_INVALID_ARG, "blocks_per_sm in [0, 32]");
     SG_CHECK(p->steps_per_round >= 0, SG_ERR_INVALID_ARG, "steps_per_round must be >= 0");
     SG_CHECK(p->max_rounds >= 0, SG_ERR_INVALID_ARG, "max_rounds must be >= 0");
+    SG_CHECK(p->direction >= SG_DIR_FORWARD && p->direction <= SG_DIR_BOTH, SG_ERR_INVALID_ARG, "bad direction %d",
+             p->direction);
     if (p->mode == SG_STREAMLINE) {
         SG_CHECK(p->max_steps >= 0 && p->max_steps < (1 << 27), SG_ERR_INVALID_ARG, "max_steps out of range");
         SG_CHECK(p->kernel == SG_KERNEL_PERSISTENT || p->kernel == SG_KERNEL_PER_SEED ||
@@ -164,6 +168,7 @@ static sg_status check_params(const sg_field *f, const sg_tracer_params *p)
         else
             SG_CHECK(f->desc.layout != SG_FIELD_GLOBAL, SG_ERR_UNSUPPORTED, "this kernel samples a bricked field");
     } else {
+        SG_CHECK(p->direction == SG_DIR_FORWARD, SG_ERR_UNSUPPORTED, "streaklines advance forward in time");
         SG_CHECK(p->inject_steps >= 1, SG_ERR_INVALID_ARG, "inject_steps must be >= 1");
         SG_CHECK(f->desc.n_slots >= 2, SG_ERR_INVALID_ARG, "streaklines need a field with >= 2 slots");
         SG_CHECK(f->desc.layout != SG_FIELD_GLOBAL, SG_ERR_UNSUPPORTED, "streaklines sample a bricked field");
@@ -178,28 +183,36 @@ static size_t tracer_layout(const sg_field *f, const sg_tracer_params *p, int64_
     const int nb = f->nb;
     if (p->mode == SG_STREAMLINE) {
         const long long W = (long long)p->max_steps + 1;
+        const int64_t lc = cap * (p->direction == SG_DIR_BOTH ? 2 : 1);   // line slots
         float *seeds = (float *)c.take(sizeof(float) * 3 * cap);
-        float *slab = (float *)c.take(sizeof(float) * 3 * (size_t)W * cap);
-        uint32_t *len = (uint32_t *)c.take(sizeof(uint32_t) * cap);
-        uint8_t *st = (uint8_t *)c.take(cap);
-        float *mg = (float *)c.take(sizeof(float) * cap);
+        float *slab = (float *)c.take(sizeof(float) * 3 * (size_t)W * lc);
+        uint32_t *len = (uint32_t *)c.take(sizeof(uint32_t) * lc);
+        uint8_t *st = (uint8_t *)c.take(lc);
+        float *mg = (float *)c.take(sizeof(float) * lc);
         Particle *q = nullptr, *o = nullptr, *pk = nullptr;
         if (p->kernel != SG_KERNEL_PER_SEED) {
-            q = (Particle *)c.take(sizeof(Particle) * cap);
-            o = (Particle *)c.take(sizeof(Particle) * cap);
-            pk = (Particle *)c.take(sizeof(Particle) * cap);
+            q = (Particle *)c.take(sizeof(Particle) * lc);
+            o = (Particle *)c.take(sizeof(Particle) * lc);
+            pk = (Particle *)c.take(sizeof(Particle) * lc);
         }
         Ctrl *ctrl = (Ctrl *)c.take(sizeof(Ctrl));
         uint32_t *bc = (uint32_t *)c.take(sizeof(uint32_t) * nb);
         uint32_t *bcur = (uint32_t *)c.take(sizeof(uint32_t) * nb);
-        int64_t *off = (int64_t *)c.take(sizeof(int64_t) * (cap + 1));
-        unsigned long long *bs = (unsigned long long *)c.take(sizeof(unsigned long long) * (cap / 4096 + 2));
+        int64_t *off = (int64_t *)c.take(sizeof(int64_t) * (lc + 1));
+        unsigned long long *bs = (unsigned long long *)c.take(sizeof(unsigned long long) * (lc / 4096 + 2));
         int64_t *tot = (int64_t *)c.take(sizeof(int64_t) * 4);
+        uint32_t *jlen = nullptr;
+        int64_t *joff = nullptr, *jtot = nullptr;
+        if (p->direction == SG_DIR_BOTH) {
+            jlen = (uint32_t *)c.take(sizeof(uint32_t) * cap);
+            joff = (int64_t *)c.take(sizeof(int64_t) * (cap + 1));
+            jtot = (int64_t *)c.take(sizeof(int64_t) * 4);
+        }
         // two staging buffers for readback into host memory, each at least one line
         size_t stage = (size_t)256 << 20;
         const size_t line_bytes = sizeof(float) * 3 * (size_t)W;
         if (stage < line_bytes) stage = line_bytes;
-        const size_t slab_bytes = sizeof(float) * 3 * (size_t)W * cap;
+        const size_t slab_bytes = sizeof(float) * 3 * (size_t)W * lc;
         if (stage > slab_bytes) stage = slab_bytes > line_bytes ? slab_bytes : line_bytes;
         stage = align_up(stage, 256);
         float *st0 = (float *)c.take(stage);
@@ -222,6 +235,9 @@ static size_t tracer_layout(const sg_field *f, const sg_tracer_params *p, int64_
             t->offsets = off;
             t->block_sums = bs;
             t->totals = tot;
+            t->join_len = jlen;
+            t->join_off = joff;
+            t->join_tot = jtot;
         }
     } else {
         const long long inj = p->inject_steps;
@@ -277,6 +293,7 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
     t->field = f;
     t->p = *p;
     t->capacity = capacity;
+    t->line_mult = (p->mode == SG_STREAMLINE && p->direction == SG_DIR_BOTH) ? 2 : 1;
     t->ws = (char *)workspace;
     t->ws_bytes = bytes;
     t->nb = f->nb;
@@ -352,6 +369,7 @@ extern "C" sg_status sg_tracer_upload_seeds(sg_tracer *t, const float *xyz, int6
         SG_CUDA(cudaMemcpyAsync(t->seeds, xyz, sizeof(float) * 3 * (size_t)n, cudaMemcpyDefault, s));
     }
     t->n_seeds = n;
+    t->n_lines = n * t->line_mult;
     t->scanned = false;
     t->traced = false;
     t->horizon = 0;
@@ -650,25 +668,25 @@ extern "C" sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t
         (st = check_out_ptr(line_source, "line_source")))
         return st;
     if (t->p.mode == SG_STREAKLINE) return launch_streak_gather(t, offsets, vertices, status, margin, line_source, s);
-    if (line_source && t->n_seeds > 0) {
-        st = launch_iota(line_source, t->n_seeds, s);
+    if (line_source && t->n_lines > 0) {
+        st = launch_iota(line_source, t->n_lines, t->n_seeds, s);
         if (st) return st;
     }
-    if (vertices && pointer_kind(vertices) == PTR_PINNED && t->n_seeds > 0) {
+    if (vertices && pointer_kind(vertices) == PTR_PINNED && t->n_lines > 0) {
         // host destination: gather chunks of lines into device staging buffers
         // and copy each to the host on the copy stream, overlapping the next
         // chunk's gather (DMA copies beat kernel stores over the host link)
         st = launch_gather_lines(t, offsets, nullptr, status, margin, s);
         if (st) return st;
-        std::vector<int64_t> off((size_t)t->n_seeds + 1);
+        std::vector<int64_t> off((size_t)t->n_lines + 1);
         SG_CUDA(cudaMemcpyAsync(off.data(), t->offsets, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost, s));
         SG_CUDA(cudaStreamSynchronize(s));
         const long long cap_v = (long long)(t->staging_bytes / (3 * sizeof(float)));
         long long a = 0;
         int k = 0;
-        while (a < t->n_seeds) {
+        while (a < t->n_lines) {
             long long b = a + 1;
-            while (b < t->n_seeds && off[b + 1] - off[a] <= cap_v) ++b;
+            while (b < t->n_lines && off[b + 1] - off[a] <= cap_v) ++b;
             const int buf = k & 1;
             SG_CUDA(cudaStreamWaitEvent(s, t->ev_copied[buf], 0));          // the buffer's last copy is done
             st = launch_gather_chunk(t, a, b, off[a], t->staging[buf], s);
@@ -687,6 +705,30 @@ extern "C" sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t
         return SG_OK;
     }
     return launch_gather_lines(t, offsets, vertices, status, margin, s);
+}
+
+extern "C" sg_status sg_tracer_get_joined(sg_tracer *t, int64_t *n_lines, int64_t *n_vertices, int64_t *offsets,
+                                          float *vertices, int64_t *seed_vertex, void *stream)
+{
+    SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
+    SG_CHECK(t->p.mode == SG_STREAMLINE && t->p.direction == SG_DIR_BOTH, SG_ERR_STATE,
+             "joined lines need a streamline tracer created with SG_DIR_BOTH");
+    SG_CUDA(cudaSetDevice(t->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    sg_status st = launch_join_scan(t, s);
+    if (st) return st;
+    const bool query = !offsets && !vertices && !seed_vertex;
+    if (query || n_lines || n_vertices) {
+        int64_t h[4];
+        SG_CUDA(cudaMemcpyAsync(h, t->join_tot, sizeof h, cudaMemcpyDeviceToHost, s));
+        SG_CUDA(cudaStreamSynchronize(s));
+        if (n_lines) *n_lines = t->n_seeds;
+        if (n_vertices) *n_vertices = t->n_seeds > 0 ? h[0] : 0;
+        if (query) return SG_OK;
+    }
+    for (const void *q : {(const void *)offsets, (const void *)vertices, (const void *)seed_vertex})
+        SG_CHECK(!q || pointer_kind(q) == PTR_DEVICE, SG_ERR_INVALID_ARG, "joined-line buffers must be device memory");
+    return launch_join(t, offsets, vertices, seed_vertex, s);
 }
 
 extern "C" sg_status sg_tracer_total_steps(sg_tracer *t, int64_t *steps, void *stream)

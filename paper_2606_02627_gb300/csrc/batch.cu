@@ -636,6 +636,8 @@ extern "C" sg_status sg_batch_submit(sg_batch *b, sg_field *f, const float *xyz,
     SG_CHECK(b && f && p && request_id, SG_ERR_INVALID_ARG, "NULL argument");
     SG_CHECK(n >= 0 && (n == 0 || xyz), SG_ERR_INVALID_ARG, "bad seeds");
     SG_CHECK(p->mode == SG_STREAMLINE, SG_ERR_UNSUPPORTED, "a batch traces streamlines");
+    SG_CHECK(p->direction == SG_DIR_FORWARD || p->direction == SG_DIR_BACKWARD, SG_ERR_UNSUPPORTED,
+             "a batch request traces one direction");
     SG_CHECK(p->dt > 0.0 && p->dt < 1e30, SG_ERR_INVALID_ARG, "dt must be > 0");
     SG_CHECK(p->max_steps >= 0 && p->max_steps < (1 << 27), SG_ERR_INVALID_ARG, "max_steps out of range");
     SG_CHECK(f->desc.layout == b->d.layout, SG_ERR_INVALID_ARG, "the field's layout differs from the batch's");
@@ -695,7 +697,7 @@ extern "C" sg_status sg_batch_submit(sg_batch *b, sg_field *f, const float *xyz,
     memset(&R, 0, sizeof R);
     R.F = field_view(f, 0);
     for (int a = 0; a < 3; ++a) {
-        R.dtc[a] = (float)(p->dt / f->desc.spacing[a]);
+        R.dtc[a] = (float)(p->dt / f->desc.spacing[a]) * (p->direction == SG_DIR_BACKWARD ? -1.0f : 1.0f);
         R.origin_d[a] = f->desc.origin[a];
         R.spacing_d[a] = f->desc.spacing[a];
     }

@@ -181,9 +181,93 @@ sg_status launch_gather_chunk(const sg_tracer *t, long long a, long long b, long
     return SG_OK;
 }
 
-sg_status launch_scan_lengths(sg_tracer *t, cudaStream_t s)
+// ------------------------------------------------------------------ bidirectional lines
+
+// Joined polyline lengths: the backward line (seed excluded) then the forward
+// line; 0 for an OUT seed (both lines empty).
+__global__ void join_len_kernel(const uint32_t *__restrict__ len, long long n, uint32_t *__restrict__ jlen)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t lf = len[i], lb = len[n + i];
+        jlen[i] = lf == 0u ? 0u : lb - 1u + lf;
+    }
+}
+
+// One warp per seed: the backward line's vertices lb-1 .. 1, then the
+// forward line's vertices 0 .. lf-1.
+__global__ void join_gather_kernel(const float *__restrict__ slab, long long W, const uint32_t *__restrict__ len,
+                                   const int64_t *__restrict__ joff, long long n, int64_t *off_out,
+                                   float *__restrict__ vertices, int64_t *seed_vertex)
+{
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned lane = threadIdx.x & 31;
+    for (long long i = warp; i < n; i += nwarps) {
+        const long long lf = len[i], lb = len[n + i];
+        const long long o = joff[i];
+        if (vertices && lf > 0) {
+            float *d = vertices + 3 * o;
+            const float *sb = slab + (n + i) * W * 3;
+            const long long nb = 3 * (lb - 1);
+            for (long long k = lane; k < nb; k += 32) {
+                const long long j = k / 3, c = k - 3 * j;
+                d[k] = __ldcs(sb + 3 * (lb - 1 - j) + c);
+            }
+            const float *sf = slab + i * W * 3;
+            for (long long k = lane; k < 3 * lf; k += 32) d[nb + k] = __ldcs(sf + k);
+        }
+        if (lane == 0) {
+            if (off_out) off_out[i] = o;
+            if (seed_vertex) seed_vertex[i] = lf > 0 ? lb - 1 : -1;
+        }
+    }
+    if (off_out && blockIdx.x == 0 && threadIdx.x == 0) off_out[n] = joff[n];
+}
+
+static sg_status launch_scan(const uint32_t *len, long long n, unsigned long long *block_sums, int64_t *totals,
+                             int64_t *offsets, cudaStream_t s)
+{
+    const long long nblocks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    if (nblocks > 0) {
+        scan_reduce_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(len, n, block_sums);
+        SG_CUDA(cudaGetLastError());
+    }
+    scan_blocks_kernel<<<1, SCAN_THREADS, 0, s>>>(block_sums, nblocks, totals, offsets, n);
+    SG_CUDA(cudaGetLastError());
+    if (nblocks > 0) {
+        scan_apply_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(len, n, block_sums, offsets);
+        SG_CUDA(cudaGetLastError());
+    }
+    return SG_OK;
+}
+
+sg_status launch_join_scan(sg_tracer *t, cudaStream_t s)
 {
     const long long n = t->n_seeds;
+    if (n > 0) {
+        join_len_kernel<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(t->line_len, n,
+                                                                                                 t->join_len);
+        SG_CUDA(cudaGetLastError());
+    }
+    return launch_scan(t->join_len, n, t->block_sums, t->join_tot, t->join_off, s);
+}
+
+sg_status launch_join(sg_tracer *t, int64_t *offsets, float *vertices, int64_t *seed_vertex, cudaStream_t s)
+{
+    const long long n = t->n_seeds;
+    if (n == 0) {
+        if (offsets) SG_CUDA(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
+        return SG_OK;
+    }
+    join_gather_kernel<<<t->ctx->sm_count * 8, 256, 0, s>>>(t->slab, (long long)t->p.max_steps + 1, t->line_len,
+                                                             t->join_off, n, offsets, vertices, seed_vertex);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+sg_status launch_scan_lengths(sg_tracer *t, cudaStream_t s)
+{
+    const long long n = t->n_lines;
     const long long nblocks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
     if (nblocks > 0) {
         scan_reduce_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(t->line_len, n, t->block_sums);
@@ -201,7 +285,7 @@ sg_status launch_scan_lengths(sg_tracer *t, cudaStream_t s)
 sg_status launch_gather_lines(sg_tracer *t, int64_t *offsets, float *vertices, uint8_t *status, float *margin,
                               cudaStream_t s)
 {
-    const long long n = t->n_seeds;
+    const long long n = t->n_lines;
     int grid = t->ctx->sm_count * 8;
     gather_lines_kernel<<<grid, 256, 0, s>>>(t->slab, (long long)t->p.max_steps + 1, t->line_len, t->offsets, n,
                                              vertices, t->line_status, status, t->line_margin, margin, offsets);

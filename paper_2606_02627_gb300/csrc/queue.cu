@@ -188,15 +188,16 @@ sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStrea
     return launch_bin_args(A, t->ctx->sm_count, s, in_graph, cond_handle, mode);
 }
 
-__global__ void iota_kernel(int32_t *dst, long long n)
+// dst[i] = i mod period (the seed of streamline i)
+__global__ void iota_kernel(int32_t *dst, long long n, long long period)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = (int32_t)i;
+        dst[i] = (int32_t)(i % period);
 }
 
-sg_status launch_iota(int32_t *dst, int64_t n, cudaStream_t s)
+sg_status launch_iota(int32_t *dst, int64_t n, int64_t period, cudaStream_t s)
 {
-    iota_kernel<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(dst, n);
+    iota_kernel<<<(unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, s>>>(dst, n, period);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }

@@ -19,6 +19,8 @@ struct LineParams {
     float *line_margin;
     long long W;                 // max_steps + 1
     long long n_lines;
+    long long n_seed;            // seeds uploaded: line l starts at seed l (l < n_seed) or l - n_seed
+    long long n_fwd;             // lines [0, n_fwd) integrate forward, the rest backward (-dt)
     float dtc[3];                // dt / spacing: cells per unit velocity
     float eps;
     float tie_cells;
@@ -31,6 +33,20 @@ struct LineParams {
 };
 
 enum { EV_NONE = 0, EV_STOP = 1, EV_APPEND = 2, EV_PARK = 3 };
+
+// The seed a line starts from, and its direction of integration (the step
+// factor dt/h negated for backward lines: exact).
+__device__ __forceinline__ long long seed_of(const LineParams &P, long long line)
+{
+    return line >= P.n_seed ? line - P.n_seed : line;
+}
+
+__device__ __forceinline__ void line_dtc(const LineParams &P, long long line, float dtc[3])
+{
+    const bool fwd = line < P.n_fwd;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dtc[a] = fwd ? P.dtc[a] : -P.dtc[a];
+}
 
 // One request of a batch (device copy).  Its lines occupy the global line
 // slots [line_base, line_base + n_lines); its vertex slabs start at float
@@ -76,8 +92,13 @@ struct sg_tracer {
     sg_context *ctx;
     sg_field *field;
     sg_tracer_params p;
-    int64_t capacity;
+    int64_t capacity;            // seeds
     int64_t n_seeds;
+    int64_t n_lines;             // n_seeds, or 2 n_seeds for SG_DIR_BOTH
+    int line_mult;               // lines per seed (1, or 2 for SG_DIR_BOTH)
+    uint32_t *join_len;          // SG_DIR_BOTH: joined polyline lengths [capacity]
+    int64_t *join_off;           // SG_DIR_BOTH: their offsets [capacity + 1]
+    int64_t *join_tot;           // SG_DIR_BOTH: totals of the joined scan [4]
     char *ws;
     size_t ws_bytes;
     int nb;
@@ -128,6 +149,8 @@ struct sg_tracer {
 namespace sg {
 
 sg_status launch_upload(sg_tracer *t, cudaStream_t s);
+sg_status launch_join_scan(sg_tracer *t, cudaStream_t s);
+sg_status launch_join(sg_tracer *t, int64_t *offsets, float *vertices, int64_t *seed_vertex, cudaStream_t s);
 sg_status launch_per_seed(sg_tracer *t, cudaStream_t s);
 sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStream_t s, bool in_graph,
                      unsigned long long cond_handle, int mode);
@@ -140,7 +163,7 @@ sg_status launch_compact_range(const uint32_t *len, long long n, const float *sl
 sg_status launch_round(sg_tracer *t, cudaStream_t s);
 sg_status prepare_round(sg_tracer *t);
 sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s);
-sg_status launch_iota(int32_t *dst, int64_t n, cudaStream_t s);
+sg_status launch_iota(int32_t *dst, int64_t n, int64_t period, cudaStream_t s);
 sg_status streak_upload(sg_tracer *t, cudaStream_t s);
 sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s);
 sg_status launch_scan_lengths(sg_tracer *t, cudaStream_t s);

@@ -483,3 +483,43 @@ def test_fx21_codes_match_numpy_rounding_and_error_bound():
         err = np.abs(codes[b][fin].astype(np.float64) * scales[b] - stored[fin])
         assert err.max() <= s_b * 2.0 ** -21
     assert np.isnan(deq[1, 2, 3]).all()
+
+
+# ---------------------------------------------------------------- backward integration
+
+def test_backward_uniform_flow_exact_line_and_exit():
+    # backward lines follow -v: the uniform-flow line runs to the lower face
+    g = unit_grid(17)
+    F = inputs.uniform_field(g, (1.0, 0.0, 0.0))
+    seed = np.array([[9.0, 5.5, 7.25]])
+    L = oracle.trace_streamlines(F, g.origin, g.spacing, seed, dt=-0.25, max_steps=500)
+    # p_n = 9 - n/4; the step from x = 0 has its first stage point at -0.125 < 0
+    assert L.status[0] == oracle.EXIT
+    assert L.length[0] == 37
+    np.testing.assert_array_equal(L.line(0)[:, 0], 9.0 - 0.25 * np.arange(37))
+    assert L.margin[0] == 0.125
+
+
+def test_backward_is_forward_in_the_negated_field():
+    # RK4 with -dt on v takes exactly the steps of RK4 with dt on -v (every
+    # stage is dt * v(P) and negation is exact), so the lines agree bit for bit
+    g = inputs.cube_grid(21)
+    F = inputs.turbulence_field(g, inputs.turbulence_modes(31, n_modes=24, kmax=3)).numpy()
+    seeds = inputs.uniform_seeds(g, 200, 31)
+    dt = 0.5 / oracle.max_speed(F, g.spacing)
+    a = oracle.trace_streamlines(F, g.origin, g.spacing, seeds, -dt, 300)
+    b = oracle.trace_streamlines(-F, g.origin, g.spacing, seeds, dt, 300)
+    np.testing.assert_array_equal(a.length, b.length)
+    np.testing.assert_array_equal(a.status, b.status)
+    np.testing.assert_array_equal(a.verts, b.verts)
+    # and a backward step undoes a forward one to RK4's local error (h^5)
+    org, sp = np.asarray(g.origin), np.asarray(g.spacing)
+    f = oracle.trace_streamlines(F, g.origin, g.spacing, seeds, dt, 1)
+    ok = np.flatnonzero(f.length == 2)
+    ends = np.stack([org + sp * f.line(i)[1] for i in ok])
+    back = oracle.trace_streamlines(F, g.origin, g.spacing, ends, -dt, 1)
+    assert (back.length == 2).all()
+    ret = np.stack([back.line(i)[1] for i in range(len(ok))])          # index space
+    start = (seeds[ok].astype(np.float64) - org) / sp
+    err = np.abs(ret - start).max()
+    assert 0 < err < 1e-3           # h = 0.5 cell: (h)^5 scale, far below a cell, yet not exact
