@@ -7,7 +7,8 @@
  *     per brick or from a global array (Sec. 3.1.1, Sec. 3.3);
  *   - seeds given as positions, each tracked by a unique ID (Sec. 3.1.2);
  *   - step / trace / getLines of the Tracer (Sec. 3.2, Fig. 4, Listing 2),
- *     in streamline or streakline mode (the Mode enumeration of Fig. 4).
+ *     in streamline, streakline or path-line mode (the Mode enumeration of
+ *     Fig. 4, with path lines added).
  *
  * Conventions
  *   - Every call returns sg_status: SG_OK (0) or a negative error.  No call
@@ -91,7 +92,13 @@ enum {
     SG_LINE_TIE = 0x80
 };
 
-enum { SG_STREAMLINE = 0, SG_STREAKLINE = 1 };
+/* Line modes (Fig. 4's Mode): streamlines in a steady field; streaklines
+ * (one release per seed per step, Sec. 3.2); path lines: every seed released
+ * once at time 0 and followed through the time-dependent field, one vertex
+ * per step (the paper notes they follow from the same machinery, Sec. 3.2).
+ * Streak and path lines advance with sg_tracer_step and sample a field whose
+ * time slices are streamed into resident slots (sg_field_stream_slice). */
+enum { SG_STREAMLINE = 0, SG_STREAKLINE = 1, SG_PATHLINE = 2 };
 
 /* Direction of streamline integration (the paper's Tracer advects forward
  * only; backward lines follow -v, the same RK4 with -dt).  With
@@ -269,10 +276,14 @@ sg_status sg_tracer_upload_seeds(sg_tracer *t, const float *xyz, int64_t n, void
 /* Advances by n_steps steps (Listing 2's step(), called n_steps times):
  * streamlines advance every active line by up to n_steps more steps;
  * streaklines advance every released particle by one step of the time-
- * dependent field and then release the next birth, n_steps times.
- * any_active (nullable, host) receives 1 if a particle can still move; when
- * it is non-NULL the call synchronises the stream.  Returns
- * SG_ERR_ROUND_LIMIT if the round cap stopped the call early. */
+ * dependent field and then release the next birth, n_steps times; path
+ * lines advance every moving line by one step of the time-dependent field
+ * (step j from time (j-1) dt to j dt), n_steps times or until max_steps.
+ * Streak and path steps need the slices of their stage times resident
+ * (SG_ERR_STATE otherwise).  any_active (nullable, host) receives 1 if a
+ * particle can still move; when it is non-NULL the call synchronises the
+ * stream.  Returns SG_ERR_ROUND_LIMIT if the round cap stopped the call
+ * early. */
 sg_status sg_tracer_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, void *stream);
 
 /* Streamlines: advances until every line has stopped (Sec. 3.2's trace()).

@@ -391,6 +391,41 @@ int or_trace_streaklines(const float *slices, int64_t n_slices, const int64_t di
     return 0;
 }
 
+/* Path lines: every seed released once at time 0 and followed through the
+ * time-dependent field (slices at times s*slice_dt, linear in time between
+ * them); step j takes the particle from time (j-1)*dt to j*dt.  The same
+ * per-line loop as a streamline with the time-dependent sampler.  Outputs as
+ * or_trace_streamlines. */
+int or_trace_pathlines(const float *slices, int64_t n_slices, const int64_t dims[3], const double origin[3],
+                       const double spacing[3], double slice_dt, const double *seeds, int64_t n, double dt,
+                       int64_t max_steps, double eps, double *verts, int32_t *len, uint8_t *status,
+                       double *margin, int nthreads)
+{
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 2 || !(spacing[a] > 0.0)) return -1;
+    if (n_slices < 2 || n < 0 || max_steps < 0 || !(slice_dt > 0.0)) return -1;
+    slices_ctx g;
+    g.F = slices;
+    memcpy(g.dims, dims, sizeof g.dims);
+    g.n_slices = n_slices;
+    g.slice_dt = slice_dt;
+    double inv_sp[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        inv_sp[a] = 1.0 / spacing[a];
+        hi[a] = (double)(dims[a] - 1);
+    }
+    set_threads(nthreads);
+    int64_t stride = 3 * (max_steps + 1);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double p0[3];
+        for (int a = 0; a < 3; ++a) p0[a] = (seeds[3 * i + a] - origin[a]) / spacing[a];
+        trace_line(slices_sampler, &g, p0, 0.0, dt, max_steps, eps, inv_sp, hi, verts + stride * i, len + i,
+                   status + i, margin + i);
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Brick decomposition and the quantised field store.
  *

@@ -59,6 +59,8 @@ def _load():
             lib.or_trace_streaklines.argtypes = [P, i64, P, P, P, d, P, i64, d, i64, i64, d, P, P, P, P,
                                                  ctypes.c_int]
             lib.or_trace_streaklines.restype = ctypes.c_int
+            lib.or_trace_pathlines.argtypes = [P, i64, P, P, P, d, P, i64, d, i64, d, P, P, P, P, ctypes.c_int]
+            lib.or_trace_pathlines.restype = ctypes.c_int
             lib.or_brick_cells.argtypes = [P, P, P]
             lib.or_brick_cells.restype = ctypes.c_int
             lib.or_owner_brick.argtypes = [P, P, P, P]
@@ -179,6 +181,29 @@ def trace_streaklines(slices, origin, spacing, slice_dt, release_world, dt, n_st
     if rc:
         raise ValueError("or_trace_streaklines: bad arguments")
     return Streaks(pos, status, steps, margin)
+
+
+def trace_pathlines(slices, origin, spacing, slice_dt, seeds_world, dt, max_steps, eps=1e-6, nthreads=0) -> Lines:
+    """Path lines through the slices (linear in time between them), FP64; see oracle.c."""
+    lib = _load()
+    S = np.ascontiguousarray(slices, dtype=np.float32)
+    if S.ndim != 5 or S.shape[4] != 3:
+        raise ValueError("slices must be [n_slices][nz][ny][nx][3]")
+    dims = np.array([S.shape[3], S.shape[2], S.shape[1]], dtype=np.int64)
+    seeds = np.ascontiguousarray(np.asarray(seeds_world, dtype=np.float64).reshape(-1, 3))
+    n = seeds.shape[0]
+    org = np.ascontiguousarray(origin, dtype=np.float64)
+    sp = np.ascontiguousarray(spacing, dtype=np.float64)
+    verts = np.zeros((n, max_steps + 1, 3), dtype=np.float64)
+    length = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.uint8)
+    margin = np.zeros(n, dtype=np.float64)
+    rc = lib.or_trace_pathlines(_p(S), S.shape[0], _p(dims), _p(org), _p(sp), float(slice_dt), _p(seeds), n,
+                                float(dt), int(max_steps), float(eps), _p(verts), _p(length), _p(status),
+                                _p(margin), int(nthreads))
+    if rc:
+        raise ValueError("or_trace_pathlines: bad arguments")
+    return Lines(verts, length, status, margin)
 
 
 def brick_cells(dims, bricks):

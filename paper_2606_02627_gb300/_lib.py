@@ -30,6 +30,7 @@ SG_LAYOUT_LINEAR, SG_LAYOUT_TILED4, SG_LAYOUT_CELL8, SG_FIELD_GLOBAL = 0, 1, 2, 
 SG_STREAMLINE, SG_STREAKLINE = 0, 1
 SG_KERNEL_PERSISTENT, SG_KERNEL_PER_SEED, SG_KERNEL_PER_STEP, SG_KERNEL_LOCKSTEP = 0, 1, 2, 3
 SG_DIR_FORWARD, SG_DIR_BACKWARD, SG_DIR_BOTH = 0, 1, 2
+SG_PATHLINE = 2
 SG_LINE_ACTIVE, SG_LINE_MAXSTEPS, SG_LINE_EXIT, SG_LINE_STAGNANT = 0, 1, 2, 3
 SG_LINE_NANFIELD, SG_LINE_OUT, SG_LINE_HALO, SG_LINE_TIE = 4, 5, 6, 0x80
 

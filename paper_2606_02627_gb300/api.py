@@ -194,7 +194,7 @@ def tracer_params(dt, max_steps=1000, mode="streamline", kernel="persistent", ep
                   max_rounds=0, drain_steps=0, direction="forward") -> L.sg_tracer_params:
     p = L.sg_tracer_params()
     call("sg_tracer_params_default", ctypes.byref(p))
-    p.mode = L.SG_STREAMLINE if mode == "streamline" else L.SG_STREAKLINE
+    p.mode = {"streamline": L.SG_STREAMLINE, "streakline": L.SG_STREAKLINE, "pathline": L.SG_PATHLINE}[mode]
     p.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     p.dt = float(dt)
     p.max_steps = int(max_steps)

@@ -147,7 +147,8 @@ extern "C" sg_status sg_tracer_params_default(sg_tracer_params *p)
 
 static sg_status check_params(const sg_field *f, const sg_tracer_params *p)
 {
-    SG_CHECK(p->mode == SG_STREAMLINE || p->mode == SG_STREAKLINE, SG_ERR_INVALID_ARG, "bad mode %d", p->mode);
+    SG_CHECK(p->mode == SG_STREAMLINE || p->mode == SG_STREAKLINE || p->mode == SG_PATHLINE, SG_ERR_INVALID_ARG,
+             "bad mode %d", p->mode);
     SG_CHECK(p->dt > 0.0 && p->dt < 1e30, SG_ERR_INVALID_ARG, "dt must be > 0");
     SG_CHECK(p->eps >= 0.0f, SG_ERR_INVALID_ARG, "eps must be >= 0");
     SG_CHECK(p->block_size >= 0 && p->block_size <= 1024 && p->block_size % 32 == 0, SG_ERR_INVALID_ARG,
@@ -167,6 +168,11 @@ static sg_status check_params(const sg_field *f, const sg_tracer_params *p)
                      "the per-seed kernel samples the global float3 layout");
         else
             SG_CHECK(f->desc.layout != SG_FIELD_GLOBAL, SG_ERR_UNSUPPORTED, "this kernel samples a bricked field");
+    } else if (p->mode == SG_PATHLINE) {
+        SG_CHECK(p->direction == SG_DIR_FORWARD, SG_ERR_UNSUPPORTED, "path lines advance forward in time");
+        SG_CHECK(p->max_steps >= 0 && p->max_steps < (1 << 27), SG_ERR_INVALID_ARG, "max_steps out of range");
+        SG_CHECK(f->desc.n_slots >= 2, SG_ERR_INVALID_ARG, "path lines need a field with >= 2 slots");
+        SG_CHECK(f->desc.layout != SG_FIELD_GLOBAL, SG_ERR_UNSUPPORTED, "path lines sample a bricked field");
     } else {
         SG_CHECK(p->direction == SG_DIR_FORWARD, SG_ERR_UNSUPPORTED, "streaklines advance forward in time");
         SG_CHECK(p->inject_steps >= 1, SG_ERR_INVALID_ARG, "inject_steps must be >= 1");
@@ -181,7 +187,7 @@ static size_t tracer_layout(const sg_field *f, const sg_tracer_params *p, int64_
 {
     Carve c{base, 0, 0};
     const int nb = f->nb;
-    if (p->mode == SG_STREAMLINE) {
+    if (p->mode == SG_STREAMLINE || p->mode == SG_PATHLINE) {
         const long long W = (long long)p->max_steps + 1;
         const int64_t lc = cap * (p->direction == SG_DIR_BOTH ? 2 : 1);   // line slots
         float *seeds = (float *)c.take(sizeof(float) * 3 * cap);
@@ -190,7 +196,7 @@ static size_t tracer_layout(const sg_field *f, const sg_tracer_params *p, int64_
         uint8_t *st = (uint8_t *)c.take(lc);
         float *mg = (float *)c.take(sizeof(float) * lc);
         Particle *q = nullptr, *o = nullptr, *pk = nullptr;
-        if (p->kernel != SG_KERNEL_PER_SEED) {
+        if (p->kernel != SG_KERNEL_PER_SEED || p->mode == SG_PATHLINE) {
             q = (Particle *)c.take(sizeof(Particle) * lc);
             o = (Particle *)c.take(sizeof(Particle) * lc);
             pk = (Particle *)c.take(sizeof(Particle) * lc);
@@ -319,6 +325,8 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
             delete t;
             return pst;
         }
+    }
+    if (t->p.mode != SG_STREAKLINE) {
         cudaError_t ce = cudaStreamCreateWithFlags(&t->copy_stream, cudaStreamNonBlocking);
         for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
             ce = cudaEventCreateWithFlags(&t->ev_gathered[k], cudaEventDisableTiming);
@@ -374,6 +382,7 @@ extern "C" sg_status sg_tracer_upload_seeds(sg_tracer *t, const float *xyz, int6
     t->traced = false;
     t->horizon = 0;
     if (t->p.mode == SG_STREAKLINE) return streak_upload(t, s);
+    if (t->p.mode == SG_PATHLINE) return path_upload(t, s);
     if (t->ctrl) SG_CUDA(cudaMemsetAsync(t->ctrl, 0, sizeof(Ctrl), s));
     return launch_upload(t, s);
 }
@@ -461,7 +470,7 @@ static sg_status run_call(sg_tracer *t, uint32_t horizon, uint32_t n_steps, cuda
 extern "C" sg_status sg_tracer_trace(sg_tracer *t, void *stream)
 {
     SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
-    SG_CHECK(t->p.mode == SG_STREAMLINE, SG_ERR_STATE, "trace() is for streamlines; streaklines use step()");
+    SG_CHECK(t->p.mode == SG_STREAMLINE, SG_ERR_STATE, "trace() is for streamlines; streak and path lines use step()");
     SG_CUDA(cudaSetDevice(t->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (t->n_seeds == 0) return SG_OK;
@@ -563,6 +572,7 @@ extern "C" sg_status sg_tracer_step(sg_tracer *t, int32_t n_steps, int32_t *any_
     SG_CUDA(cudaSetDevice(t->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (t->p.mode == SG_STREAKLINE) return streak_step(t, n_steps, any_active, s);
+    if (t->p.mode == SG_PATHLINE) return path_step(t, n_steps, any_active, s);
     SG_CHECK(t->p.kernel != SG_KERNEL_PER_SEED, SG_ERR_UNSUPPORTED, "the per-seed kernel only traces to the end");
     uint64_t target = (uint64_t)t->horizon + (uint64_t)n_steps;
     if (target > (uint64_t)t->p.max_steps) target = (uint64_t)t->p.max_steps;

@@ -11,7 +11,7 @@
 #include <math.h>
 #include <string.h>
 
-#include "tracer.cuh"
+#include "rk4.cuh"
 
 namespace sg {
 
@@ -78,8 +78,50 @@ __device__ __forceinline__ float dom_out(const DevField &F, const int q[3], cons
     return fmaxf(out_axis(q[0], g[0], F.nm1[0]), fmaxf(out_axis(q[1], g[1], F.nm1[1]), out_axis(q[2], g[2], F.nm1[2])));
 }
 
-// One RK4 step of every released, live particle (stage times t, t+dt/2,
-// t+dt/2, t+dt use stage slots 0, 1, 1, 2).
+// One RK4 step of a particle through the time-dependent field (stage times
+// t, t+dt/2, t+dt/2, t+dt use stage slots 0, 1, 1, 2).  On success updates
+// (c, f) and returns SG_LINE_ACTIVE; else the stop status (margin set for
+// EXIT and STAGNANT), the particle left at P0.
+template <int DT>
+__device__ __forceinline__ int rk4_time(const StreakParams &P, int layout, int c[3], float f[3], float &margin)
+{
+    int q[3];
+    float g[3];
+    float k1[3], k2[3], k3[3], k4[3];
+    float3 v = sample_time<DT>(P, layout, 0, c, f);
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    if (sp < P.eps) {
+        margin = (P.eps - sp) / P.eps;
+        return SG_LINE_STAGNANT;
+    }
+    k1[0] = v.x * P.dtc[0]; k1[1] = v.y * P.dtc[1]; k1[2] = v.z * P.dtc[2];
+    for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k1[a], c[a], q[a], g[a]);
+    if (!dom(P.F, q, g)) { margin = dom_out(P.F, q, g); return SG_LINE_EXIT; }
+    v = sample_time<DT>(P, layout, 1, q, g);
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    k2[0] = v.x * P.dtc[0]; k2[1] = v.y * P.dtc[1]; k2[2] = v.z * P.dtc[2];
+    for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k2[a], c[a], q[a], g[a]);
+    if (!dom(P.F, q, g)) { margin = dom_out(P.F, q, g); return SG_LINE_EXIT; }
+    v = sample_time<DT>(P, layout, 1, q, g);
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    k3[0] = v.x * P.dtc[0]; k3[1] = v.y * P.dtc[1]; k3[2] = v.z * P.dtc[2];
+    for (int a = 0; a < 3; ++a) locate(f[a], k3[a], c[a], q[a], g[a]);
+    if (!dom(P.F, q, g)) { margin = dom_out(P.F, q, g); return SG_LINE_EXIT; }
+    v = sample_time<DT>(P, layout, 2, q, g);
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    k4[0] = v.x * P.dtc[0]; k4[1] = v.y * P.dtc[1]; k4[2] = v.z * P.dtc[2];
+    for (int a = 0; a < 3; ++a)
+        locate(f[a], (k1[a] + k4[a] + 2.0f * (k2[a] + k3[a])) * (1.0f / 6.0f), c[a], q[a], g[a]);
+    if (!dom(P.F, q, g)) { margin = dom_out(P.F, q, g); return SG_LINE_EXIT; }
+    for (int a = 0; a < 3; ++a) {
+        c[a] = q[a];
+        f[a] = g[a];
+    }
+    return SG_LINE_ACTIVE;
+}
+
+// One RK4 step of every released, live particle.
 template <int DT>
 __global__ void streak_advect_kernel(const __grid_constant__ StreakParams P, int layout)
 {
@@ -90,62 +132,110 @@ __global__ void streak_advect_kernel(const __grid_constant__ StreakParams P, int
         Particle pr = P.state[k];
         int c[3] = {pr.cx, pr.cy, pr.cz};
         float f[3] = {pr.fx, pr.fy, pr.fz};
-        int q[3];
-        float g[3];
-        int st = SG_LINE_ACTIVE;
         float margin = INFINITY;
-        float3 v = sample_time<DT>(P, layout, 0, c, f);
-        float k1[3], k2[3], k3[3], k4[3];
-        if (bad3(v)) st = SG_LINE_NANFIELD;
+        const int st = rk4_time<DT>(P, layout, c, f, margin);
         if (st == SG_LINE_ACTIVE) {
-            const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
-            if (sp < P.eps) {
-                st = SG_LINE_STAGNANT;
-                margin = (P.eps - sp) / P.eps;
-            }
-        }
-        if (st == SG_LINE_ACTIVE) {
-            k1[0] = v.x * P.dtc[0]; k1[1] = v.y * P.dtc[1]; k1[2] = v.z * P.dtc[2];
-            for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k1[a], c[a], q[a], g[a]);
-            if (!dom(P.F, q, g)) { st = SG_LINE_EXIT; margin = dom_out(P.F, q, g); }
-        }
-        if (st == SG_LINE_ACTIVE) {
-            v = sample_time<DT>(P, layout, 1, q, g);
-            if (bad3(v)) st = SG_LINE_NANFIELD;
-        }
-        if (st == SG_LINE_ACTIVE) {
-            k2[0] = v.x * P.dtc[0]; k2[1] = v.y * P.dtc[1]; k2[2] = v.z * P.dtc[2];
-            for (int a = 0; a < 3; ++a) locate(f[a], 0.5f * k2[a], c[a], q[a], g[a]);
-            if (!dom(P.F, q, g)) { st = SG_LINE_EXIT; margin = dom_out(P.F, q, g); }
-        }
-        if (st == SG_LINE_ACTIVE) {
-            v = sample_time<DT>(P, layout, 1, q, g);
-            if (bad3(v)) st = SG_LINE_NANFIELD;
-        }
-        if (st == SG_LINE_ACTIVE) {
-            k3[0] = v.x * P.dtc[0]; k3[1] = v.y * P.dtc[1]; k3[2] = v.z * P.dtc[2];
-            for (int a = 0; a < 3; ++a) locate(f[a], k3[a], c[a], q[a], g[a]);
-            if (!dom(P.F, q, g)) { st = SG_LINE_EXIT; margin = dom_out(P.F, q, g); }
-        }
-        if (st == SG_LINE_ACTIVE) {
-            v = sample_time<DT>(P, layout, 2, q, g);
-            if (bad3(v)) st = SG_LINE_NANFIELD;
-        }
-        if (st == SG_LINE_ACTIVE) {
-            k4[0] = v.x * P.dtc[0]; k4[1] = v.y * P.dtc[1]; k4[2] = v.z * P.dtc[2];
-            for (int a = 0; a < 3; ++a)
-                locate(f[a], (k1[a] + k4[a] + 2.0f * (k2[a] + k3[a])) * (1.0f / 6.0f), c[a], q[a], g[a]);
-            if (!dom(P.F, q, g)) { st = SG_LINE_EXIT; margin = dom_out(P.F, q, g); }
-        }
-        if (st == SG_LINE_ACTIVE) {
-            pr.cx = q[0]; pr.cy = q[1]; pr.cz = q[2];
-            pr.fx = g[0]; pr.fy = g[1]; pr.fz = g[2];
+            pr.cx = c[0]; pr.cy = c[1]; pr.cz = c[2];
+            pr.fx = f[0]; pr.fy = f[1]; pr.fz = f[2];
             pr.step += 1;
             P.state[k] = pr;
         } else {
             P.status[k] = (uint8_t)st;
             P.margin[k] = margin;
         }
+    }
+}
+
+// Path lines: every live particle takes step `step` (from time (step-1) dt)
+// and writes its vertex; the line stops at its first failed step or when it
+// reaches max_steps.  *active counts the lines still moving afterwards.
+struct PathLines {
+    Particle *state;
+    float *slab;
+    uint32_t *len;
+    uint8_t *status;
+    float *margin;
+    long long W;
+    long long n;
+    uint32_t max_steps;
+    float tie_cells, tie_eps_rel;
+    unsigned long long *active;
+};
+
+template <int DT>
+__global__ void path_advect_kernel(const __grid_constant__ StreakParams P, int layout, PathLines L, uint32_t step)
+{
+    unsigned long long moving = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += (long long)gridDim.x * blockDim.x) {
+        if (L.status[i] != SG_LINE_ACTIVE) continue;
+        if (step > L.max_steps) {
+            L.status[i] = SG_LINE_MAXSTEPS;
+            continue;
+        }
+        Particle pr = L.state[i];
+        int c[3] = {pr.cx, pr.cy, pr.cz};
+        float f[3] = {pr.fx, pr.fy, pr.fz};
+        float margin = INFINITY;
+        const int st = rk4_time<DT>(P, layout, c, f, margin);
+        if (st == SG_LINE_ACTIVE) {
+            pr.cx = c[0]; pr.cy = c[1]; pr.cz = c[2];
+            pr.fx = f[0]; pr.fy = f[1]; pr.fz = f[2];
+            pr.step = step;
+            L.state[i] = pr;
+            float *o = L.slab + (i * L.W + step) * 3;
+            o[0] = fmaf(P.F.spacing[0], (float)c[0] + f[0], P.F.origin[0]);
+            o[1] = fmaf(P.F.spacing[1], (float)c[1] + f[1], P.F.origin[1]);
+            o[2] = fmaf(P.F.spacing[2], (float)c[2] + f[2], P.F.origin[2]);
+            L.len[i] = step + 1;
+            if (step >= L.max_steps) L.status[i] = SG_LINE_MAXSTEPS;
+            else ++moving;
+        } else {
+            L.status[i] = stop_code_t(st, margin, L.tie_cells, L.tie_eps_rel);
+            L.margin[i] = margin;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) moving += __shfl_xor_sync(SG_FULL_MASK, moving, o);
+    if ((threadIdx.x & 31) == 0 && moving) atomicAdd(L.active, moving);
+}
+
+// Path-line start: particle state, first vertex (the seed), status.
+__global__ void path_init_kernel(const float *seeds, long long n, DevField F, double ox, double oy, double oz,
+                                 double hx, double hy, double hz, PathLines L)
+{
+    const double org[3] = {ox, oy, oz}, sp[3] = {hx, hy, hz};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double p[3];
+        bool inside = true;
+        for (int a = 0; a < 3; ++a) {
+            p[a] = ((double)seeds[3 * i + a] - org[a]) / sp[a];
+            inside = inside && p[a] >= 0.0 && p[a] <= (double)F.nm1[a];
+        }
+        L.margin[i] = INFINITY;
+        if (!inside) {
+            L.len[i] = 0;
+            L.status[i] = SG_LINE_OUT;
+            continue;
+        }
+        Particle pr;
+        int c[3];
+        float f[3];
+        for (int a = 0; a < 3; ++a) {
+            const double fl = floor(p[a]);
+            c[a] = (int)fl;
+            f[a] = (float)(p[a] - fl);
+            if (f[a] >= 1.0f) { f[a] = 0.0f; c[a] += 1; }
+        }
+        pr.cx = c[0]; pr.cy = c[1]; pr.cz = c[2];
+        pr.fx = f[0]; pr.fy = f[1]; pr.fz = f[2];
+        pr.line = (uint32_t)i;
+        pr.step = 0;
+        L.state[i] = pr;
+        float *o = L.slab + i * L.W * 3;
+        o[0] = seeds[3 * i];
+        o[1] = seeds[3 * i + 1];
+        o[2] = seeds[3 * i + 2];
+        L.len[i] = 1;
+        L.status[i] = L.max_steps == 0 ? SG_LINE_MAXSTEPS : SG_LINE_ACTIVE;
     }
 }
 
@@ -334,44 +424,68 @@ sg_status streak_upload(sg_tracer *t, cudaStream_t s)
 }
 
 // Slice pair of time t: s = ceil(t/slice_dt) - 1 (>= 0), alpha = t/slice_dt - s.
+// A time within a relative 1e-9 of a slice time is taken as that slice time,
+// so that a step whose dt is a multiple or a fraction of slice_dt never asks
+// for a slice whose weight is a rounding error.
 static void slice_pair(double t, double sdt, int *s_out, double *alpha_out)
 {
-    const double u = t / sdt;
+    double u = t / sdt;
+    const double r = nearbyint(u);
+    if (fabs(u - r) <= 1e-9 * fmax(1.0, fabs(u))) u = r;
     long long s = (long long)ceil(u) - 1;
     if (s < 0) s = 0;
     *s_out = (int)s;
     *alpha_out = u - (double)s;
 }
 
-sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s)
+// The resident slots that step j's three stage times sample (into P), after
+// the stream has waited for each slot's copy; need[][] lists the slices.
+static sg_status stage_slots(sg_tracer *t, int j, StreakParams &P, int need[3][2], cudaStream_t s)
 {
     sg_field *f = t->field;
     const double dt = t->p.dt, sdt = f->desc.slice_dt;
+    const double t0 = (double)(j - 1) * dt;
+    const double times[3] = {t0, t0 + 0.5 * dt, t0 + dt};
+    for (int st = 0; st < 3; ++st) {
+        int sl;
+        double al;
+        slice_pair(times[st], sdt, &sl, &al);
+        // a slice with weight zero is not needed: sample the other one twice
+        need[st][0] = al == 1.0 ? sl + 1 : sl;
+        need[st][1] = al == 0.0 ? sl : sl + 1;
+        for (int h = 0; h < 2; ++h) {
+            const int slice = need[st][h];
+            const int slot = slice % f->desc.n_slots;
+            SG_CHECK(f->slot_slice[slot] == slice, SG_ERR_STATE,
+                     "step %d needs time slice %d, which is not resident (slot %d holds %d)", j, slice, slot,
+                     f->slot_slice[slot]);
+            SG_CUDA(cudaStreamWaitEvent(s, f->slot_ready[slot], 0));
+            P.slot_data[2 * st + h] = f->slot_data[slot];
+            P.slot_scale[2 * st + h] = f->slot_scales[slot];
+        }
+        P.alpha[st] = (float)al;
+    }
+    return SG_OK;
+}
+
+// Later streams into the slots a step sampled wait for the step.
+static sg_status release_slots(sg_tracer *t, const int need[3][2], cudaStream_t s)
+{
+    sg_field *f = t->field;
+    for (int st = 0; st < 3; ++st)
+        for (int h = 0; h < 2; ++h) SG_CUDA(cudaEventRecord(f->slot_used[need[st][h] % f->desc.n_slots], s));
+    return SG_OK;
+}
+
+sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s)
+{
+    sg_field *f = t->field;
     for (int i = 0; i < n_steps; ++i) {
         const int j = t->steps_done + 1;
-        const double t0 = (double)(j - 1) * dt;
-        const double times[3] = {t0, t0 + 0.5 * dt, t0 + dt};
         StreakParams P = streak_params(t);
         int need[3][2];
-        for (int st = 0; st < 3; ++st) {
-            int sl;
-            double al;
-            slice_pair(times[st], sdt, &sl, &al);
-            // a slice with weight zero is not needed: sample the other one twice
-            need[st][0] = al == 1.0 ? sl + 1 : sl;
-            need[st][1] = al == 0.0 ? sl : sl + 1;
-            for (int h = 0; h < 2; ++h) {
-                const int slice = need[st][h];
-                const int slot = slice % f->desc.n_slots;
-                SG_CHECK(f->slot_slice[slot] == slice, SG_ERR_STATE,
-                         "step %d needs time slice %d, which is not resident (slot %d holds %d)", j, slice, slot,
-                         f->slot_slice[slot]);
-                SG_CUDA(cudaStreamWaitEvent(s, f->slot_ready[slot], 0));
-                P.slot_data[2 * st + h] = f->slot_data[slot];
-                P.slot_scale[2 * st + h] = f->slot_scales[slot];
-            }
-            P.alpha[st] = (float)al;
-        }
+        sg_status st = stage_slots(t, j, P, need, s);
+        if (st) return st;
         const long long total = t->n_seeds * (long long)t->p.inject_steps;
         if (total > 0) {
             with_dtype(f->desc.dtype, [&](auto D) {
@@ -383,9 +497,8 @@ sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaSt
                 SG_CUDA(cudaGetLastError());
             }
         }
-        // later streams into these slots wait for this step
-        for (int st = 0; st < 3; ++st)
-            for (int h = 0; h < 2; ++h) SG_CUDA(cudaEventRecord(f->slot_used[need[st][h] % f->desc.n_slots], s));
+        st = release_slots(t, need, s);
+        if (st) return st;
         if (j < t->p.inject_steps) t->births = j + 1;
         t->steps_done = j;
     }
@@ -393,6 +506,75 @@ sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaSt
     if (any_active) {
         SG_CUDA(cudaStreamSynchronize(s));
         *any_active = t->n_seeds > 0 ? 1 : 0;
+    }
+    return SG_OK;
+}
+
+// ------------------------------------------------------------------ path lines
+
+static PathLines path_lines(const sg_tracer *t)
+{
+    PathLines L;
+    L.state = t->q;
+    L.slab = t->slab;
+    L.len = t->line_len;
+    L.status = t->line_status;
+    L.margin = t->line_margin;
+    L.W = (long long)t->p.max_steps + 1;
+    L.n = t->n_lines;
+    L.max_steps = (uint32_t)t->p.max_steps;
+    L.tie_cells = t->p.tie_cells;
+    L.tie_eps_rel = t->p.tie_eps_rel;
+    L.active = reinterpret_cast<unsigned long long *>(t->totals + 3);
+    return L;
+}
+
+sg_status path_upload(sg_tracer *t, cudaStream_t s)
+{
+    t->steps_done = 0;
+    const long long n = t->n_lines;
+    if (n == 0) return SG_OK;
+    const sg_field *f = t->field;
+    const sg_field_desc &d = f->desc;
+    path_init_kernel<<<grid_for(t, n), 256, 0, s>>>(t->seeds, n, field_view(f, 0), d.origin[0], d.origin[1],
+                                                    d.origin[2], d.spacing[0], d.spacing[1], d.spacing[2],
+                                                    path_lines(t));
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+// Advances every moving path line by up to n_steps steps (time slices of
+// each step must be resident); *any_active: lines still moving.
+sg_status path_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s)
+{
+    sg_field *f = t->field;
+    const PathLines L = path_lines(t);
+    bool ran = false;
+    for (int i = 0; i < n_steps && t->steps_done < t->p.max_steps; ++i) {
+        const int j = t->steps_done + 1;
+        StreakParams P = streak_params(t);
+        int need[3][2];
+        sg_status st = stage_slots(t, j, P, need, s);
+        if (st) return st;
+        SG_CUDA(cudaMemsetAsync(L.active, 0, sizeof(unsigned long long), s));
+        if (L.n > 0) {
+            with_dtype(f->desc.dtype, [&](auto D) {
+                path_advect_kernel<decltype(D)::value><<<grid_for(t, L.n), 256, 0, s>>>(P, f->desc.layout, L,
+                                                                                      (uint32_t)j);
+            });
+            SG_CUDA(cudaGetLastError());
+        }
+        st = release_slots(t, need, s);
+        if (st) return st;
+        t->steps_done = j;
+        ran = true;
+    }
+    t->scanned = false;
+    if (any_active) {
+        unsigned long long moving = 0;
+        if (ran) SG_CUDA(cudaMemcpyAsync(&moving, L.active, sizeof moving, cudaMemcpyDeviceToHost, s));
+        SG_CUDA(cudaStreamSynchronize(s));
+        *any_active = (ran && moving > 0) ? 1 : 0;
     }
     return SG_OK;
 }

@@ -165,6 +165,8 @@ sg_status prepare_round(sg_tracer *t);
 sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s);
 sg_status launch_iota(int32_t *dst, int64_t n, int64_t period, cudaStream_t s);
 sg_status streak_upload(sg_tracer *t, cudaStream_t s);
+sg_status path_upload(sg_tracer *t, cudaStream_t s);
+sg_status path_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s);
 sg_status streak_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s);
 sg_status launch_scan_lengths(sg_tracer *t, cudaStream_t s);
 sg_status launch_gather_lines(sg_tracer *t, int64_t *offsets, float *vertices, uint8_t *status, float *margin,

@@ -523,3 +523,44 @@ def test_backward_is_forward_in_the_negated_field():
     start = (seeds[ok].astype(np.float64) - org) / sp
     err = np.abs(ret - start).max()
     assert 0 < err < 1e-3           # h = 0.5 cell: (h)^5 scale, far below a cell, yet not exact
+
+
+# ---------------------------------------------------------------- path lines
+
+def test_pathlines_in_steady_field_are_streamlines():
+    n = 32
+    g = unit_grid(n)
+    c = (n - 1) / 2.0
+    F = inputs.rotation_field(g, center=(c, c, c))
+    slices = np.stack([F] * 5)
+    seeds = np.array([[20.0, 15.5, 3.0], [10.25, 18.0, 30.0], [-1.0, 2.0, 2.0]])
+    dt = 0.07
+    P = oracle.trace_pathlines(slices, g.origin, g.spacing, 3 * dt, seeds, dt, 40)
+    L = oracle.trace_streamlines(F, g.origin, g.spacing, seeds, dt, 40)
+    np.testing.assert_array_equal(P.length, L.length)
+    np.testing.assert_array_equal(P.status, L.status)
+    for i in range(3):
+        np.testing.assert_allclose(P.line(i), L.line(i), atol=1e-12)
+
+
+def test_pathlines_exact_for_linear_in_time_flow():
+    # v(t) = a + (b - a) t / sdt on [0, sdt], b afterwards, the same at every
+    # point: RK4 integrates a polynomial of degree <= 3 in t exactly, so the
+    # vertices are the closed-form trajectory to rounding
+    n = 64
+    g = unit_grid(n)
+    a = np.array([0.5, 0.25, 0.0])
+    bvel = np.array([1.0, -0.5, 0.75])
+    slices = np.stack([inputs.uniform_field(g, a), inputs.uniform_field(g, bvel), inputs.uniform_field(g, bvel)])
+    dt, sdt = 0.25, 0.5
+    x0 = np.array([[10.0, 40.0, 5.0]])
+    P = oracle.trace_pathlines(slices, g.origin, g.spacing, sdt, x0, dt, 12)
+    assert P.status[0] == oracle.MAXSTEPS and P.length[0] == 13
+
+    def X(t):
+        if t <= sdt:
+            return a * t + (bvel - a) * t * t / (2 * sdt)
+        return X(sdt) + bvel * (t - sdt)
+
+    for j in range(13):
+        np.testing.assert_allclose(P.line(0)[j], x0[0] + X(j * dt), atol=1e-12)
