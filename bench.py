@@ -314,10 +314,18 @@ def run_serve(args, rank, world, local):
         seed += 2
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
+    # schedule: the autotuner's pick on the largest FP32 field (a 64k-seed sample, cached per shape)
+    from paper_2606_02627_gb300 import autotune
+    big = fields[6]
+    sample = torch.from_numpy(inputs.uniform_seeds(big.grid, 1 << 16, 99)).to(dev)
+    sched = autotune.tune(ctx, big.field, sample, big.dt, 1000, first=1 << 14,
+                          cache=os.path.join(tempfile.gettempdir(), "streamgb_autotune.json"))
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info(dev)
     slab = int(min(free * 0.6, 160e9))
     srv = serving.Server(ctx, fields, max_lines=8 << 20, slab_bytes=slab, rounds_per_launch=4,
-                         max_requests=1024)
+                         max_requests=1024, schedule=sched)
     base = serving.make_requests(fields, args.requests, rate_hz=1.0, seed=4 + 1000 * rank)
     # capacity: the same requests all arriving at once
     burst = [serving.Request(r.idx, 0.0, r.field, r.seeds, r.max_steps, r.shape) for r in base]
@@ -333,7 +341,7 @@ def run_serve(args, rank, world, local):
            "config": {"workload": "serving: 8 resident fields {64,128,256,512}^3 x {FP32,BF16} turbulence, Poisson "
                                   f"requests ({args.requests}) of 100-1M seeds (box/rake), max steps 10-5000, "
                                   f"rate = 70 % of measured capacity ({rate:.1f}/s)",
-                      "rounds_per_launch": 4, "slab_pool_bytes": slab},
+                      "rounds_per_launch": 4, "slab_pool_bytes": slab, "schedule": sched},
            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
            "particle_steps_per_s": st["particle_steps_per_s"], "particle_steps": st["particle_steps"],
            "capacity": {"requests_per_s": len(burst) / cap["makespan_s"],

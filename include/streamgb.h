@@ -391,9 +391,10 @@ typedef struct {
     int32_t max_fields;      /* distinct fields used by requests (<= 64) */
     int32_t max_bricks;      /* bricks summed over those fields (<= 65536) */
     int32_t layout;          /* field layout of every request's field */
-    int32_t block_size;      /* schedule of the persistent kernel (0 = default) */
-    int32_t blocks_per_sm;
+    int32_t block_size;      /* schedule of the persistent kernel (0 = default), */
+    int32_t blocks_per_sm;   /* as the fields of sg_tracer_params                */
     int32_t steps_per_round;
+    int32_t drain_steps;
 } sg_batch_desc;
 
 /* Device bytes of a batch (slab pool, line arrays, queues, request table,

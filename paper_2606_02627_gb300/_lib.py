@@ -53,7 +53,7 @@ class sg_batch_desc(ctypes.Structure):
     _fields_ = [("max_lines", ctypes.c_int64), ("slab_bytes", ctypes.c_int64), ("max_requests", ctypes.c_int32),
                 ("max_fields", ctypes.c_int32), ("max_bricks", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("block_size", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("steps_per_round", ctypes.c_int32)]
+                ("steps_per_round", ctypes.c_int32), ("drain_steps", ctypes.c_int32)]
 
 
 class StreamGBError(RuntimeError):

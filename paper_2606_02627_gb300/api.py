@@ -324,7 +324,7 @@ class Batch:
     between runs and leave when their last line stops."""
 
     def __init__(self, ctx: Context, max_lines: int, slab_bytes: int, layout="cell8", max_requests=1024,
-                 max_fields=16, max_bricks=4096, block_size=0, blocks_per_sm=0, steps_per_round=0):
+                 max_fields=16, max_bricks=4096, block_size=0, blocks_per_sm=0, steps_per_round=0, drain_steps=0):
         self.ctx = ctx
         d = L.sg_batch_desc()
         d.max_lines = int(max_lines)
@@ -336,6 +336,7 @@ class Batch:
         d.block_size = int(block_size)
         d.blocks_per_sm = int(blocks_per_sm)
         d.steps_per_round = int(steps_per_round)
+        d.drain_steps = int(drain_steps)
         self.desc = d
         nbytes = ctypes.c_size_t()
         call("sg_batch_required_bytes", ctx.h, ctypes.byref(d), ctypes.byref(nbytes))

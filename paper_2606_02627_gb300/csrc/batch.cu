@@ -26,6 +26,7 @@ struct BatchParams {
     uint8_t *line_status;
     float *line_margin;
     uint32_t steps_per_round;
+    uint32_t drain_steps;
 };
 
 // A brick of any storage type: the typed view is made at the call.
@@ -168,6 +169,236 @@ __global__ void __launch_bounds__(256) batch_round_kernel(const __grid_constant_
         }
         if (ev != EV_NONE) active = false;
     }
+}
+
+// The same round with the lanes of a warp decoupled (CELL8 layout), as the
+// tracer's round_async_kernel: each lane keeps the cell record of its current
+// sample point in its own shared-memory slot (8 chunks of 16 B, enough for
+// FP32; the 8-byte formats use 4), fetches another with cp.async completing
+// on its own mbarrier, and runs one RK4 stage per pass; the storage type of
+// each lane's request selects the decode.  Stage arithmetic as rk4_bricked's.
+constexpr int BATCH_SLOT_CHUNKS = 8;
+// Consecutive passes a lane may wait for one record copy (each pass takes at
+// least ~100 cycles: well over a second in all), as in the tracer's kernel.
+constexpr unsigned BATCH_COPY_WAIT_PASSES = 1u << 24;
+
+__device__ __forceinline__ float3 interp_slot(int dtype, const uint4 *slots, unsigned nthr, unsigned tid, float fx,
+                                              float fy, float fz, bool &bad)
+{
+    switch (dtype) {
+    case SG_BF16: {
+        Record<SG_BF16> R;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) R.r[k] = slots[k * nthr + tid];
+        return interp_record<SG_BF16>(R, fx, fy, fz, bad);
+    }
+    case SG_F16: {
+        Record<SG_F16> R;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) R.r[k] = slots[k * nthr + tid];
+        return interp_record<SG_F16>(R, fx, fy, fz, bad);
+    }
+    case SG_FX21: {
+        Record<SG_FX21> R;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) R.r[k] = slots[k * nthr + tid];
+        return interp_record<SG_FX21>(R, fx, fy, fz, bad);
+    }
+    default: {
+        Record<SG_F32> R;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) R.r[k] = slots[k * nthr + tid];
+        return interp_record<SG_F32>(R, fx, fy, fz, bad);
+    }
+    }
+}
+
+__global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant__ BatchParams P)
+{
+    extern __shared__ uint4 slots[];                       // [8][blockDim] chunks, then blockDim barriers
+    const unsigned tid = threadIdx.x, nthr = blockDim.x;
+    const unsigned lane = tid & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + BATCH_SLOT_CHUNKS * nthr) + tid);
+    const uint32_t slot = smem_addr(slots + tid);
+    mbar_init(bar, 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+
+    const uint32_t q_count = P.ctrl->q_count;
+    bool active = false, pending = false;
+    bool drained = q_count == 0;
+    uint32_t drain_left = P.drain_steps >= 0x20000000u ? 0xffffffffu : P.drain_steps * 4u;   // 4 passes a step
+    unsigned parity = 0, waited = 0;
+    int c[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+    float f[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};
+    float k1[3] = {0.f, 0.f, 0.f}, k2[3] = {0.f, 0.f, 0.f}, k3[3] = {0.f, 0.f, 0.f};
+    float ds[3] = {0.f, 0.f, 0.f};
+    uint32_t line = 0, step = 0, here = 0, stage = 0, r = 0, max_steps = 0;
+    uint32_t held = 0xffffffffu, wanted = 0;
+    int dtype = SG_F32;
+    float eps = 0.f;
+    float *vslab = nullptr;
+    const ReqDev *R = P.reqs;
+    BrickAny br;
+    br.data = nullptr;
+    br.scale = 1.0f;
+    for (int a = 0; a < 3; ++a) br.lo[a] = br.hi[a] = 0;
+
+    auto fetch = [&]() {
+        const DevField &F = R->F;
+        const int sx = q[0] - br.lo[0] + 1, sy = q[1] - br.lo[1] + 1, sz = q[2] - br.lo[2] + 1;
+        const uint32_t cell = (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
+        if (cell != held) {
+            const int nch = dtype == SG_F32 ? 8 : 4;
+            const uint4 *src = reinterpret_cast<const uint4 *>(br.data) + (long long)cell * nch;
+            for (int k = 0; k < nch; ++k) cp_async16(slot + k * nthr * 16u, src + k);
+            cp_async_arrive(bar);
+            held = 0xffffffffu;
+            wanted = cell;
+            pending = true;
+            waited = 0;
+        }
+    };
+
+    while (true) {
+        const unsigned need = __ballot_sync(SG_FULL_MASK, !active);
+        if (need && !drained) {
+            const int leader = __ffs(need) - 1;
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(&P.ctrl->q_head, (uint32_t)__popc(need));
+            base = __shfl_sync(SG_FULL_MASK, base, leader);
+            if (base + (uint32_t)__popc(need) >= q_count) drained = true;
+            if (!active) {
+                const uint32_t my = base + __popc(need & lt);
+                if (my < q_count) {
+                    load_particle(P.q + my, c, f, line, step);
+                    r = P.line_req[line];
+                    R = P.reqs + r;
+                    dtype = R->dtype;
+                    max_steps = R->max_steps;
+                    eps = R->eps;
+                    vslab = P.slab + R->slab_base + (long long)(line - R->line_base) * R->W * 3;
+                    brick_any(R->F, dtype, c, br);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        ds[a] = dtype == SG_F32 ? R->dtc[a] : __fmul_rn(R->dtc[a], br.scale);
+                        q[a] = c[a];
+                        g[a] = f[a];
+                    }
+                    active = true;
+                    here = 0;
+                    stage = 0;
+                    held = 0xffffffffu;
+                    fetch();
+                }
+            }
+        }
+        if (__ballot_sync(SG_FULL_MASK, active) == 0) break;
+        if (drained) {
+            if (drain_left == 0) here = P.steps_per_round;
+            else --drain_left;
+        }
+        bool gave_up = false;
+        if (pending) {
+            if (mbar_done(bar, parity)) {
+                held = wanted;
+                parity ^= 1u;
+                pending = false;
+            } else if (++waited >= BATCH_COPY_WAIT_PASSES) {
+                atomicOr(&P.ctrl->err, CTRL_ERR_TIMEOUT);
+                active = false;
+                pending = false;
+                gave_up = true;
+            }
+        }
+        if (__any_sync(SG_FULL_MASK, gave_up)) drained = true;
+
+        int ev = EV_NONE, st = SG_LINE_ACTIVE;
+        float margin = INFINITY;
+        bool run = active && !pending;
+        if (run && stage == 0) {
+            if (step >= max_steps) {
+                ev = EV_STOP;
+                st = SG_LINE_MAXSTEPS;
+                run = false;
+            } else if (here >= P.steps_per_round) {
+                ev = EV_APPEND;
+                run = false;
+            }
+        }
+        if (run) {
+            const DevField &F = R->F;
+            bool bad;
+            const float3 v = interp_slot(dtype, slots, nthr, tid, g[0], g[1], g[2], bad);
+            float sp = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
+            if (dtype != SG_F32) sp = __fmul_rn(sp, br.scale);
+            const float k[3] = {__fmul_rn(v.x, ds[0]), __fmul_rn(v.y, ds[1]), __fmul_rn(v.z, ds[2])};
+            const bool last = stage == 3;
+            const float w = stage < 2 ? 0.5f : 1.0f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float fin =
+                    __fmul_rn(__fadd_rn(__fadd_rn(k1[a], k[a]), __fmul_rn(2.0f, __fadd_rn(k2[a], k3[a]))), 1.0f / 6.0f);
+                locate(f[a], last ? fin : w * k[a], c[a], q[a], g[a]);
+                k1[a] = stage == 0 ? k[a] : k1[a];
+                k2[a] = stage == 1 ? k[a] : k2[a];
+                k3[a] = stage == 2 ? k[a] : k3[a];
+            }
+            if (bad) {
+                st = SG_LINE_NANFIELD;
+            } else if (stage == 0 && sp < eps) {
+                margin = (eps - sp) / eps;
+                st = SG_LINE_STAGNANT;
+            } else if (!in_domain(F, q, g)) {
+                margin = out_dist(F, q, g);
+                st = SG_LINE_EXIT;
+            } else if (!last && ((unsigned)(q[0] - br.lo[0] + 1) > (unsigned)(F.S[0] - 2) ||
+                                 (unsigned)(q[1] - br.lo[1] + 1) > (unsigned)(F.S[1] - 2) ||
+                                 (unsigned)(q[2] - br.lo[2] + 1) > (unsigned)(F.S[2] - 2))) {
+                st = SG_LINE_HALO;
+            }
+            bool go = st == SG_LINE_ACTIVE;
+            if (!go) ev = EV_STOP;
+            if (go && last) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    c[a] = q[a];
+                    f[a] = g[a];
+                }
+                ++step;
+                ++here;
+                float *o = vslab + 3ll * step;
+                st_na(o, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
+                st_na(o + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
+                st_na(o + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
+                if (step >= max_steps) {
+                    ev = EV_STOP;
+                    st = SG_LINE_MAXSTEPS;
+                    go = false;
+                } else if (c[0] < br.lo[0] || c[0] >= br.hi[0] || c[1] < br.lo[1] || c[1] >= br.hi[1] ||
+                           c[2] < br.lo[2] || c[2] >= br.hi[2]) {
+                    ev = EV_APPEND;
+                    go = false;
+                } else {
+                    go = here < P.steps_per_round;
+                }
+            }
+            stage = last ? 0 : stage + 1;
+            if (go) fetch();
+        }
+        if (__any_sync(SG_FULL_MASK, ev != EV_NONE)) {
+            warp_append(ev == EV_APPEND, P.o, &P.ctrl->o_count, c, f, line, step);
+            if (ev == EV_STOP) {
+                P.line_len[line] = step + 1;
+                P.line_status[line] = stop_code_t(st, margin, R->tie_cells, R->tie_eps_rel);
+                P.line_margin[line] = margin;
+                atomicSub(P.active + r, 1u);
+            }
+            if (ev != EV_NONE) active = false;
+        }
+    }
+    cp_async_wait_all();
 }
 
 // Seeds of request r -> particles appended to the outgoing buffer, first
@@ -423,6 +654,8 @@ static sg_status check_desc(const sg_batch_desc *d)
     return SG_OK;
 }
 
+static size_t batch_async_smem(int block) { return (size_t)block * (BATCH_SLOT_CHUNKS * 16 + 8); }
+
 static BatchParams batch_params(const sg_batch *b)
 {
     BatchParams P;
@@ -436,7 +669,10 @@ static BatchParams batch_params(const sg_batch *b)
     P.line_len = b->line_len;
     P.line_status = b->line_status;
     P.line_margin = b->line_margin;
-    P.steps_per_round = (uint32_t)(b->d.steps_per_round > 0 ? b->d.steps_per_round : 128);
+    P.steps_per_round = (uint32_t)(b->d.steps_per_round > 0 ? b->d.steps_per_round
+                                                            : (b->d.layout == SG_LAYOUT_CELL8 ? 256 : 128));
+    const int ds = b->d.drain_steps;
+    P.drain_steps = ds < 0 ? 0x7fffffffu : (ds > 0 ? (uint32_t)ds : (b->d.layout == SG_LAYOUT_CELL8 ? 128u : 0x7fffffffu));
     return P;
 }
 
@@ -462,6 +698,11 @@ static BinArgs batch_bin_args(const sg_batch *b)
 static sg_status launch_batch_round(const sg_batch *b, cudaStream_t s)
 {
     BatchParams P = batch_params(b);
+    if (b->d.layout == SG_LAYOUT_CELL8) {
+        batch_async_kernel<<<b->grid, b->block, batch_async_smem(b->block), s>>>(P);
+        SG_CUDA(cudaGetLastError());
+        return SG_OK;
+    }
     bool ok = with_layout(b->d.layout, [&](auto Lay) {
         batch_round_kernel<decltype(Lay)::value><<<b->grid, b->block, 0, s>>>(P);
     });
@@ -577,7 +818,9 @@ extern "C" sg_status sg_batch_create(sg_context *ctx, const sg_batch_desc *desc,
     b->next_brick = 0;
     b->scanned_id = -1;
     b->block = desc->block_size > 0 ? desc->block_size : 256;
-    const int per_sm = desc->blocks_per_sm > 0 ? desc->blocks_per_sm : (512 + b->block - 1) / b->block;
+    // resident threads per SM as for a tracer: 768 with decoupled lanes (CELL8), else 512
+    const int threads_per_sm = desc->layout == SG_LAYOUT_CELL8 ? 768 : 512;
+    const int per_sm = desc->blocks_per_sm > 0 ? desc->blocks_per_sm : (threads_per_sm + b->block - 1) / b->block;
     b->grid = ctx->sm_count * per_sm;
     b->graph = nullptr;
     b->exec = nullptr;
@@ -585,7 +828,17 @@ extern "C" sg_status sg_batch_create(sg_context *ctx, const sg_batch_desc *desc,
     if (e == cudaSuccess) e = cudaMemset(b->brick_count, 0, sizeof(uint32_t) * desc->max_bricks);
     if (e == cudaSuccess) e = cudaMemset(b->active, 0, sizeof(uint32_t) * desc->max_requests);
     if (e == cudaSuccess) {
-        with_layout(desc->layout, [&](auto Lay) { e = batch_prefer_l1<decltype(Lay)::value>(); });
+        if (desc->layout == SG_LAYOUT_CELL8) {
+            const size_t smem = batch_async_smem(b->block);
+            e = cudaFuncSetAttribute(batch_async_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const size_t total = (smem + 1024) * (size_t)per_sm;
+            int pct = (int)((total * 100 + 228 * 1024 - 1) / (228 * 1024));
+            if (pct > 100) pct = 100;
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(batch_async_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        } else {
+            with_layout(desc->layout, [&](auto Lay) { e = batch_prefer_l1<decltype(Lay)::value>(); });
+        }
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -748,8 +1001,14 @@ extern "C" sg_status sg_batch_finished(sg_batch *b, int64_t *ids, int32_t cap, i
     SG_CUDA(cudaSetDevice(b->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<uint32_t> act(b->req.size());
+    Ctrl c;
     SG_CUDA(cudaMemcpyAsync(act.data(), b->active, sizeof(uint32_t) * act.size(), cudaMemcpyDeviceToHost, s));
+    SG_CUDA(cudaMemcpyAsync(&c, b->ctrl, sizeof c, cudaMemcpyDeviceToHost, s));
     SG_CUDA(cudaStreamSynchronize(s));
+    if (c.err & CTRL_ERR_TIMEOUT) {
+        set_error("a record copy of the batch kernel did not complete in time");
+        return SG_ERR_TIMEOUT;
+    }
     int32_t k = 0;
     for (size_t i = 0; i < b->req.size() && k < cap; ++i) {
         ReqHost &r = b->req[i];
