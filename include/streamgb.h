@@ -341,6 +341,58 @@ sg_status sg_tracer_get_joined(sg_tracer *t, int64_t *n_lines, int64_t *n_vertic
  * the particle-steps/s metric).  Synchronous. */
 sg_status sg_tracer_total_steps(sg_tracer *t, int64_t *steps, void *stream);
 
+/* ------------------------------------------------- partition over data (POD) */
+
+/* The paper's data-parallel mode (Sec. 3.1.2, Listing 2): the bricks of the
+ * field are owned by ranks (one GPU each); a rank advects the particles of
+ * its own bricks, and the particles that leave them are forwarded to the
+ * owning ranks between rounds (emitOutgoing + an all-to-all exchange), until
+ * a reduction finds no particle left anywhere.  These calls are the rank-local
+ * side; the exchange and the reduction are the caller's (NCCL or gloo
+ * all-to-all-v, paper_2606_02627_gb300/pod.py).  Records are the library's
+ * 32-byte particle records (fraction 3 x f32, line u32, cell 3 x i32, step
+ * u32), exchanged as opaque bytes between tracers with the same field
+ * geometry and parameters.  Lines are assembled by merging every rank's line
+ * buffers (sg_tracer_line_buffers): slab by elementwise minimum (each vertex
+ * is written by one rank, the others hold +inf), length and status by
+ * maximum, margin by minimum.  Synchronous where stated. */
+
+/* Before sg_tracer_upload_seeds: brick_owner (host, one entry per brick of
+ * the field, linear brick index (bz * By + by) * Bx + bx) gives each brick's
+ * rank in [0, world); this tracer is rank `rank`; world <= 64.  Every rank
+ * then uploads every seed (each keeps the seeds in its own bricks); trace and
+ * step are refused while a partition is set (SG_ERR_STATE). */
+sg_status sg_tracer_pod_setup(sg_tracer *t, const int32_t *brick_owner, int32_t rank, int32_t world);
+
+/* After the upload: sorts this rank's particles into its local queue;
+ * *local_count (host, nullable) receives its length.  Synchronous. */
+sg_status sg_tracer_pod_begin(sg_tracer *t, int64_t *local_count, void *stream);
+
+/* One round over the local queue, then the sort of the round's outgoing
+ * particles: the local queue of the next round, and one export segment per
+ * other rank.  local_count (host, nullable) and export_counts (host, world
+ * entries, nullable; 0 for this rank) receive the sizes.  Synchronous. */
+sg_status sg_tracer_pod_round(sg_tracer *t, int64_t *local_count, int64_t *export_counts, void *stream);
+
+/* Copies the export segment of rank `dest` (export_counts[dest] records of
+ * 32 B) into records (device).  Call for every destination before any
+ * import of the same round. */
+sg_status sg_tracer_pod_export(sg_tracer *t, int32_t dest, void *records, void *stream);
+
+/* Appends count records (device, 32 B each, all in this rank's bricks) to
+ * the local queue of the next round. */
+sg_status sg_tracer_pod_import(sg_tracer *t, const void *records, int64_t count, void *stream);
+
+/* Length of the local queue (host bookkeeping, no synchronisation). */
+sg_status sg_tracer_pod_queued(const sg_tracer *t, int64_t *count);
+
+/* Device pointers of the tracer's line buffers inside its workspace (each
+ * nullable): slab (n_lines x max_vertices x 3 floats), length (u32),
+ * status (u8), margin (f32).  For merging the ranks' partial lines; the next
+ * sg_tracer_get_lines rescans them. */
+sg_status sg_tracer_line_buffers(sg_tracer *t, float **slab, uint32_t **length, uint8_t **status, float **margin,
+                                 int64_t *n_lines, int64_t *max_vertices);
+
 /* ------------------------------------------------------- seed-shape kernels */
 
 /* Seed points from control shapes, generated on the device (the low-level

@@ -97,6 +97,14 @@ SIGNATURES = {
     "sg_tracer_total_steps": ([P, ctypes.POINTER(i64), P], i32),
     "sg_tracer_get_joined": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P], i32),
     "sg_seeds_rake": ([P, P, i64, P, P], i32),
+    "sg_tracer_pod_setup": ([P, P, i32, i32], i32),
+    "sg_tracer_pod_begin": ([P, ctypes.POINTER(i64), P], i32),
+    "sg_tracer_pod_round": ([P, ctypes.POINTER(i64), P, P], i32),
+    "sg_tracer_pod_export": ([P, i32, P, P], i32),
+    "sg_tracer_pod_import": ([P, P, i64, P], i32),
+    "sg_tracer_pod_queued": ([P, ctypes.POINTER(i64)], i32),
+    "sg_tracer_line_buffers": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                ctypes.POINTER(i64), ctypes.POINTER(i64)], i32),
     "sg_seeds_plane": ([P, P, P, i64, i64, P, P], i32),
     "sg_seeds_box": ([P, P, i64, ctypes.c_uint64, ctypes.c_uint64, P, P], i32),
     "sg_lines_compact_static": ([P, i64, P, i64, P, P, P], i32),

@@ -307,6 +307,63 @@ class Tracer:
         call("sg_tracer_total_steps", self.h, ctypes.byref(n), _stream(stream))
         return n.value
 
+    # -- partition over data (see pod.py for the exchange between ranks)
+
+    def pod_setup(self, brick_owner, rank: int, world: int):
+        owner = np.ascontiguousarray(np.asarray(brick_owner, dtype=np.int32))
+        call("sg_tracer_pod_setup", self.h, _ptr(owner), int(rank), int(world))
+        self.pod_world = int(world)
+
+    def pod_begin(self, stream=None) -> int:
+        n = ctypes.c_int64()
+        call("sg_tracer_pod_begin", self.h, ctypes.byref(n), _stream(stream))
+        return n.value
+
+    def pod_round(self, stream=None):
+        """One round; returns (local queue length, export counts per rank)."""
+        n = ctypes.c_int64()
+        ex = np.zeros(self.pod_world, dtype=np.int64)
+        call("sg_tracer_pod_round", self.h, ctypes.byref(n), _ptr(ex), _stream(stream))
+        return n.value, ex
+
+    def pod_export(self, dest: int, count: int, stream=None) -> torch.Tensor:
+        """The export segment for rank dest as a uint8 tensor of count x 32 bytes (device)."""
+        out = torch.empty(max(int(count), 1) * 32, dtype=torch.uint8, device=f"cuda:{self.ctx.device}")
+        call("sg_tracer_pod_export", self.h, int(dest), _ptr(out), _stream(stream))
+        return out[:int(count) * 32]
+
+    def pod_import(self, records: torch.Tensor, stream=None):
+        records = records.contiguous()
+        assert records.dtype == torch.uint8 and records.numel() % 32 == 0
+        self._imported = records                 # alive until the copy is done
+        call("sg_tracer_pod_import", self.h, _ptr(records), records.numel() // 32, _stream(stream))
+
+    def pod_queued(self) -> int:
+        n = ctypes.c_int64()
+        call("sg_tracer_pod_queued", self.h, ctypes.byref(n))
+        return n.value
+
+    def line_buffers(self):
+        """Views (torch, device) of the tracer's line buffers: slab [n_lines, W, 3],
+        length [n_lines] int32 (uint32 bits), status [n_lines] uint8, margin [n_lines]."""
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        nl = ctypes.c_int64()
+        w = ctypes.c_int64()
+        call("sg_tracer_line_buffers", self.h, *[ctypes.byref(x) for x in ptrs], ctypes.byref(nl), ctypes.byref(w))
+        base = self.workspace.data_ptr()
+
+        def view(ptr, nbytes, dtype, shape):
+            off = ptr.value - base
+            assert 0 <= off and off + nbytes <= self.workspace.numel()
+            return self.workspace[off:off + nbytes].view(dtype).view(shape)
+
+        n, W = nl.value, w.value
+        slab = view(ptrs[0], n * W * 12, torch.float32, (n, W, 3))
+        length = view(ptrs[1], n * 4, torch.int32, (n,))
+        status = view(ptrs[2], n, torch.uint8, (n,))
+        margin = view(ptrs[3], n * 4, torch.float32, (n,))
+        return slab, length, status, margin
+
     def close(self):
         if getattr(self, "h", None):
             L.lib().sg_tracer_destroy(self.h)

@@ -202,8 +202,12 @@ static size_t tracer_layout(const sg_field *f, const sg_tracer_params *p, int64_
             pk = (Particle *)c.take(sizeof(Particle) * lc);
         }
         Ctrl *ctrl = (Ctrl *)c.take(sizeof(Ctrl));
-        uint32_t *bc = (uint32_t *)c.take(sizeof(uint32_t) * nb);
-        uint32_t *bcur = (uint32_t *)c.take(sizeof(uint32_t) * nb);
+        // binning keys: the bricks, or (partition over data) the local bricks
+        // plus one export key per rank (at most 64 ranks)
+        uint32_t *bc = (uint32_t *)c.take(sizeof(uint32_t) * (nb + 64));
+        uint32_t *bcur = (uint32_t *)c.take(sizeof(uint32_t) * (nb + 64));
+        int *kmap = (int *)c.take(sizeof(int) * nb);
+        uint32_t *kstart = (uint32_t *)c.take(sizeof(uint32_t) * 64);
         int64_t *off = (int64_t *)c.take(sizeof(int64_t) * (lc + 1));
         unsigned long long *bs = (unsigned long long *)c.take(sizeof(unsigned long long) * (lc / 4096 + 2));
         int64_t *tot = (int64_t *)c.take(sizeof(int64_t) * 4);
@@ -238,6 +242,8 @@ static size_t tracer_layout(const sg_field *f, const sg_tracer_params *p, int64_
             t->ctrl = ctrl;
             t->brick_count = bc;
             t->brick_cursor = bcur;
+            t->pod_key_map = kmap;
+            t->pod_key_start = kstart;
             t->offsets = off;
             t->block_sums = bs;
             t->totals = tot;
@@ -339,7 +345,7 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
     }
     cudaError_t e = cudaMemset(t->ctrl ? (void *)t->ctrl : (void *)t->totals, 0,
                                t->ctrl ? sizeof(Ctrl) : sizeof(int64_t) * 4);
-    if (e == cudaSuccess && t->brick_count) e = cudaMemset(t->brick_count, 0, sizeof(uint32_t) * t->nb);
+    if (e == cudaSuccess && t->brick_count) e = cudaMemset(t->brick_count, 0, sizeof(uint32_t) * (t->nb + 64));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         delete t;
@@ -384,6 +390,12 @@ extern "C" sg_status sg_tracer_upload_seeds(sg_tracer *t, const float *xyz, int6
     if (t->p.mode == SG_STREAKLINE) return streak_upload(t, s);
     if (t->p.mode == SG_PATHLINE) return path_upload(t, s);
     if (t->ctrl) SG_CUDA(cudaMemsetAsync(t->ctrl, 0, sizeof(Ctrl), s));
+    if (t->pod_world > 0) {
+        // every rank's slab starts at +inf so that the ranks' partial lines
+        // merge by an elementwise minimum (each vertex written by one rank)
+        sg_status st = launch_fill_inf(t->slab, 3 * (t->p.max_steps + 1ll) * t->n_lines, s);
+        if (st) return st;
+    }
     return launch_upload(t, s);
 }
 
@@ -471,6 +483,7 @@ extern "C" sg_status sg_tracer_trace(sg_tracer *t, void *stream)
 {
     SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
     SG_CHECK(t->p.mode == SG_STREAMLINE, SG_ERR_STATE, "trace() is for streamlines; streak and path lines use step()");
+    SG_CHECK(t->pod_world == 0, SG_ERR_STATE, "a partitioned tracer advances with the sg_tracer_pod_* calls");
     SG_CUDA(cudaSetDevice(t->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     if (t->n_seeds == 0) return SG_OK;
@@ -493,6 +506,7 @@ extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int3
 {
     SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
     SG_CHECK(t->p.mode == SG_STREAMLINE, SG_ERR_STATE, "trace() is for streamlines");
+    SG_CHECK(t->pod_world == 0, SG_ERR_STATE, "a partitioned tracer advances with the sg_tracer_pod_* calls");
     SG_CUDA(cudaSetDevice(t->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
@@ -573,6 +587,7 @@ extern "C" sg_status sg_tracer_step(sg_tracer *t, int32_t n_steps, int32_t *any_
     cudaStream_t s = (cudaStream_t)stream;
     if (t->p.mode == SG_STREAKLINE) return streak_step(t, n_steps, any_active, s);
     if (t->p.mode == SG_PATHLINE) return path_step(t, n_steps, any_active, s);
+    SG_CHECK(t->pod_world == 0, SG_ERR_STATE, "a partitioned tracer advances with the sg_tracer_pod_* calls");
     SG_CHECK(t->p.kernel != SG_KERNEL_PER_SEED, SG_ERR_UNSUPPORTED, "the per-seed kernel only traces to the end");
     uint64_t target = (uint64_t)t->horizon + (uint64_t)n_steps;
     if (target > (uint64_t)t->p.max_steps) target = (uint64_t)t->p.max_steps;

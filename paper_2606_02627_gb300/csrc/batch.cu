@@ -692,6 +692,9 @@ static BinArgs batch_bin_args(const sg_batch *b)
     A.nb = b->d.max_bricks;
     A.line_req = b->line_req;
     A.reqs = b->reqs;
+    A.key_map = nullptr;
+    A.n_local = A.nb;
+    A.key_start = nullptr;
     return A;
 }
 

@@ -24,7 +24,8 @@ __device__ __forceinline__ int brick_key(const BinArgs &A, uint32_t line, int cx
     const int bx = min(cx / A.n[0], A.B[0] - 1);
     const int by = min(cy / A.n[1], A.B[1] - 1);
     const int bz = min(cz / A.n[2], A.B[2] - 1);
-    return (bz * A.B[1] + by) * A.B[0] + bx;
+    const int b = (bz * A.B[1] + by) * A.B[0] + bx;
+    return A.key_map ? A.key_map[b] : b;
 }
 
 // Histogram of destination bricks (shared-memory counters when they fit).
@@ -81,12 +82,14 @@ __global__ void bin_scan_kernel(BinArgs A)
         if (b < A.nb) {
             A.brick_cursor[b] = before;
             A.brick_count[b] = 0;
+            if (b == A.n_local) A.ctrl->q_count = before;           // the local keys' records
+            if (b >= A.n_local && A.key_start) A.key_start[b - A.n_local] = before;
         }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry = before + v;
         __syncthreads();
     }
-    if (threadIdx.x == 0) A.ctrl->q_count = carry;
+    if (threadIdx.x == 0 && A.n_local >= A.nb) A.ctrl->q_count = carry;
 }
 
 // Scatter each record to its brick's segment; lanes with the same brick share
@@ -185,7 +188,45 @@ sg_status launch_bin(sg_tracer *t, Particle *src, uint32_t *src_count, cudaStrea
         A.B[a] = t->field->geom.B[a];
     }
     A.nb = t->nb;
+    A.key_map = nullptr;
+    A.n_local = t->nb;
+    A.key_start = nullptr;
+    if (t->pod_world > 0) {
+        A.key_map = t->pod_key_map;
+        A.n_local = t->pod_local;
+        A.nb = t->pod_local + t->pod_world;
+        A.key_start = t->pod_key_start;
+    }
     return launch_bin_args(A, t->ctx->sm_count, s, in_graph, cond_handle, mode);
+}
+
+__global__ void fill_inf_kernel(float *dst, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = INFINITY;
+}
+
+sg_status launch_fill_inf(float *dst, long long n, cudaStream_t s)
+{
+    if (n <= 0) return SG_OK;
+    fill_inf_kernel<<<(unsigned)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, s>>>(dst, n);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+__global__ void set_q_count_kernel(Ctrl *ctrl, uint32_t n)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        ctrl->q_count = n;
+        ctrl->q_head = 0;
+    }
+}
+
+sg_status launch_set_q_count(Ctrl *ctrl, uint32_t n, cudaStream_t s)
+{
+    set_q_count_kernel<<<1, 32, 0, s>>>(ctrl, n);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
 }
 
 // dst[i] = i mod period (the seed of streamline i)

@@ -84,6 +84,12 @@ struct BinArgs {
     int nb;                      // number of keys
     const uint32_t *line_req;    // batch: request of each line slot (else NULL)
     const ReqDev *reqs;
+    // partition over data (bricks owned by ranks): key = key_map[brick]; keys
+    // [0, n_local) are this rank's bricks, the rest one per destination rank
+    // (exports); the round's queue is the local keys' part
+    const int *key_map;          // NULL: key = brick
+    int n_local;                 // == nb without a key map
+    uint32_t *key_start;         // start of every export key's segment [nb - n_local]
 };
 
 }  // namespace sg
@@ -140,6 +146,15 @@ struct sg_tracer {
     int grid;
     uint32_t horizon;            // step horizon of the next call
     bool traced;
+    // partition over data: this rank advects the particles of its own bricks
+    int pod_world;               // 0: every brick is local
+    int pod_rank;
+    int pod_local;               // bricks this rank owns (local binning keys)
+    int *pod_key_map;            // device [nb]
+    uint32_t *pod_key_start;     // device [pod_world]
+    int64_t pod_queued;          // records in the local queue (host copy)
+    int64_t pod_export_start[64];
+    int64_t pod_export_count[64];
     // CUDA graph of the round loop
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -164,6 +179,8 @@ sg_status launch_round(sg_tracer *t, cudaStream_t s);
 sg_status prepare_round(sg_tracer *t);
 sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s);
 sg_status launch_iota(int32_t *dst, int64_t n, int64_t period, cudaStream_t s);
+sg_status launch_fill_inf(float *dst, long long n, cudaStream_t s);
+sg_status launch_set_q_count(Ctrl *ctrl, uint32_t n, cudaStream_t s);
 sg_status streak_upload(sg_tracer *t, cudaStream_t s);
 sg_status path_upload(sg_tracer *t, cudaStream_t s);
 sg_status path_step(sg_tracer *t, int32_t n_steps, int32_t *any_active, cudaStream_t s);
