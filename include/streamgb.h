@@ -393,6 +393,50 @@ sg_status sg_tracer_pod_queued(const sg_tracer *t, int64_t *count);
 sg_status sg_tracer_line_buffers(sg_tracer *t, float **slab, uint32_t **length, uint8_t **status, float **margin,
                                  int64_t *n_lines, int64_t *max_vertices);
 
+/* ------------------------------------------------------ unstructured fields */
+
+/* The second field type of Sec. 3.3: an unstructured mesh of tetrahedra,
+ * pyramids, prisms (wedges) and hexahedra with the velocity at its vertices,
+ * interpolated with each cell's isoparametric shape functions (VTK vertex
+ * orders: tet 0-3; pyramid base 0-3, apex 4; wedge triangles 0-2 and 3-5;
+ * hexahedron bottom 0-3, top 4-7).  A point lies in a cell when the
+ * parametric solution of sum N_i(r) x_i = p (Newton's method in FP32) maps
+ * back onto p and lies in the cell's reference domain within tau.  Cells are
+ * found through a bounding volume hierarchy built on the host at creation
+ * (median splits, at most 4 cells per leaf).  Steady streamlines in world
+ * coordinates: RK4 of Listing 1, one thread per seed; a stage point or new
+ * position in no cell stops the line (EXIT, margin = how far outside the
+ * particle's cell, in parametric units). */
+typedef struct sg_umesh sg_umesh;
+enum { SG_CELL_TET = 4, SG_CELL_PYRAMID = 5, SG_CELL_PRISM = 6, SG_CELL_HEX = 8 };
+
+/* Workspace bytes of a mesh of n_cells cells (256 B per cell record, 64 B per
+ * cell of hierarchy, 4 B of index). */
+sg_status sg_umesh_required_bytes(int64_t n_cells, size_t *bytes);
+
+/* vertices, velocity: host, n_vertices x 3 floats (world); cell_vertices,
+ * cell_offsets (n_cells + 1), cell_types (SG_CELL_*, the vertex count): host;
+ * tau: containment tolerance (0: 1e-5); workspace: device, 256-byte aligned,
+ * sg_umesh_required_bytes, kept alive by the caller.  Synchronous (the
+ * hierarchy is built on the host).  SG_ERR_INVALID_ARG on a bad type, count
+ * or index. */
+sg_status sg_umesh_create(sg_context *ctx, const float *vertices, const float *velocity, int64_t n_vertices,
+                          const int32_t *cell_vertices, const int64_t *cell_offsets, const uint8_t *cell_types,
+                          int64_t n_cells, float tau, void *workspace, size_t bytes, sg_umesh **out);
+sg_status sg_umesh_destroy(sg_umesh *m);
+
+/* Velocity at n world points (device, 3 floats each; NaN where no cell
+ * contains the point) and the containing cell's index (device, nullable, -1
+ * for none).  Asynchronous. */
+sg_status sg_umesh_sample(sg_umesh *m, const float *points, int64_t n, float *velocity, int64_t *cell, void *stream);
+
+/* Streamlines from n seeds (device, world): line i's vertices go to slab +
+ * 3 i (max_steps + 1) (device), its vertex count to length[i], its status
+ * (SG_LINE_*, tie bit for EXIT margins < 1e-3) and margin likewise (all
+ * device).  Compact with sg_lines_compact_static.  Asynchronous. */
+sg_status sg_umesh_trace(sg_umesh *m, const float *seeds, int64_t n, double dt, int32_t max_steps, float eps,
+                         float *slab, uint32_t *length, uint8_t *status, float *margin, void *stream);
+
 /* ------------------------------------------------------- seed-shape kernels */
 
 /* Seed points from control shapes, generated on the device (the low-level

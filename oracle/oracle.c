@@ -427,6 +427,275 @@ int or_trace_pathlines(const float *slices, int64_t n_slices, const int64_t dims
 }
 
 /* ------------------------------------------------------------------------ */
+/* Unstructured fields (the second field type of Sec. 3.3): cells are
+ * tetrahedra (4 vertices), pyramids (5), prisms (6) and hexahedra (8), with
+ * the VTK vertex orders; velocity is given at the vertices and interpolated
+ * with the cell's isoparametric shape functions N_i(r):
+ *   tet      1-r-s-t, r, s, t                       (r, s, t >= 0, r+s+t <= 1)
+ *   pyramid  (1-r)(1-s)(1-t), r(1-s)(1-t), rs(1-t), (1-r)s(1-t), t
+ *                                                      (r, s, t in [0, 1])
+ *   prism    (1-r-s)(1-t), r(1-t), s(1-t), (1-r-s)t, rt, st
+ *                                                      (r, s >= 0, r+s <= 1, t in [0, 1])
+ *   hex      (1-r)(1-s)(1-t), r(1-s)(1-t), rs(1-t), (1-r)s(1-t),
+ *            (1-r)(1-s)t, r(1-s)t, rst, (1-r)st        (r, s, t in [0, 1])
+ * A point p lies in a cell if the parametric solution of sum N_i(r) x_i = p
+ * (Newton's method from the cell's centre) satisfies the cell's inequalities
+ * within tau.  Point location: the cell found for the particle's previous
+ * sample is tried first, then every cell in index order (brute force).
+ * Streamlines: the same RK4 steps as a grid field, in world coordinates; a
+ * stage point or new position in no cell stops the line (EXIT) with margin =
+ * how far outside (parametric) the particle's current cell it lies.        */
+
+typedef struct {
+    const double *X;      /* vertices, n_vertices x 3 world */
+    const double *V;      /* velocity at the vertices */
+    const int32_t *idx;   /* cell vertex lists */
+    const int64_t *off;   /* cell c: idx[off[c] .. off[c+1]) */
+    const uint8_t *type;  /* 4, 5, 6, 8 */
+    int64_t n_cells;
+    double tau;
+    const int64_t *vc_off;   /* cells around each vertex (search order only) */
+    const int64_t *vc;
+} umesh;
+
+static void shape_fn(int type, const double r[3], double N[8], double dN[8][3])
+{
+    const double a = r[0], b = r[1], c = r[2];
+    switch (type) {
+    case 4:
+        N[0] = 1.0 - a - b - c; N[1] = a; N[2] = b; N[3] = c;
+        for (int i = 0; i < 4; ++i) for (int k = 0; k < 3; ++k) dN[i][k] = 0.0;
+        dN[0][0] = dN[0][1] = dN[0][2] = -1.0;
+        dN[1][0] = 1.0; dN[2][1] = 1.0; dN[3][2] = 1.0;
+        break;
+    case 5:
+        N[0] = (1 - a) * (1 - b) * (1 - c); N[1] = a * (1 - b) * (1 - c);
+        N[2] = a * b * (1 - c); N[3] = (1 - a) * b * (1 - c); N[4] = c;
+        dN[0][0] = -(1 - b) * (1 - c); dN[0][1] = -(1 - a) * (1 - c); dN[0][2] = -(1 - a) * (1 - b);
+        dN[1][0] = (1 - b) * (1 - c);  dN[1][1] = -a * (1 - c);       dN[1][2] = -a * (1 - b);
+        dN[2][0] = b * (1 - c);        dN[2][1] = a * (1 - c);        dN[2][2] = -a * b;
+        dN[3][0] = -b * (1 - c);       dN[3][1] = (1 - a) * (1 - c);  dN[3][2] = -(1 - a) * b;
+        dN[4][0] = 0.0;                dN[4][1] = 0.0;                dN[4][2] = 1.0;
+        break;
+    case 6:
+        N[0] = (1 - a - b) * (1 - c); N[1] = a * (1 - c); N[2] = b * (1 - c);
+        N[3] = (1 - a - b) * c;       N[4] = a * c;       N[5] = b * c;
+        dN[0][0] = -(1 - c); dN[0][1] = -(1 - c); dN[0][2] = -(1 - a - b);
+        dN[1][0] = (1 - c);  dN[1][1] = 0.0;      dN[1][2] = -a;
+        dN[2][0] = 0.0;      dN[2][1] = (1 - c);  dN[2][2] = -b;
+        dN[3][0] = -c;       dN[3][1] = -c;       dN[3][2] = (1 - a - b);
+        dN[4][0] = c;        dN[4][1] = 0.0;      dN[4][2] = a;
+        dN[5][0] = 0.0;      dN[5][1] = c;        dN[5][2] = b;
+        break;
+    default:
+        N[0] = (1 - a) * (1 - b) * (1 - c); N[1] = a * (1 - b) * (1 - c);
+        N[2] = a * b * (1 - c);             N[3] = (1 - a) * b * (1 - c);
+        N[4] = (1 - a) * (1 - b) * c;       N[5] = a * (1 - b) * c;
+        N[6] = a * b * c;                   N[7] = (1 - a) * b * c;
+        dN[0][0] = -(1 - b) * (1 - c); dN[0][1] = -(1 - a) * (1 - c); dN[0][2] = -(1 - a) * (1 - b);
+        dN[1][0] = (1 - b) * (1 - c);  dN[1][1] = -a * (1 - c);       dN[1][2] = -a * (1 - b);
+        dN[2][0] = b * (1 - c);        dN[2][1] = a * (1 - c);        dN[2][2] = -a * b;
+        dN[3][0] = -b * (1 - c);       dN[3][1] = (1 - a) * (1 - c);  dN[3][2] = -(1 - a) * b;
+        dN[4][0] = -(1 - b) * c;       dN[4][1] = -(1 - a) * c;       dN[4][2] = (1 - a) * (1 - b);
+        dN[5][0] = (1 - b) * c;        dN[5][1] = -a * c;             dN[5][2] = a * (1 - b);
+        dN[6][0] = b * c;              dN[6][1] = a * c;              dN[6][2] = a * b;
+        dN[7][0] = -b * c;             dN[7][1] = (1 - a) * c;        dN[7][2] = (1 - a) * b;
+        break;
+    }
+}
+
+/* How far (parametric) r lies outside the cell's reference domain; <= 0 inside. */
+static double param_violation(int type, const double r[3])
+{
+    double v = -INFINITY;
+    for (int k = 0; k < 3; ++k) v = fmax(v, -r[k]);
+    if (type == 4) v = fmax(v, r[0] + r[1] + r[2] - 1.0);
+    else if (type == 6) { v = fmax(v, r[0] + r[1] - 1.0); v = fmax(v, r[2] - 1.0); }
+    else for (int k = 0; k < 3; ++k) v = fmax(v, r[k] - 1.0);
+    return v;
+}
+
+/* Parametric coordinates of p in cell c (Newton's method); returns the
+ * violation of the cell's inequalities (<= tau: inside). */
+static double cell_param(const umesh *m, int64_t c, const double p[3], double r[3])
+{
+    const int type = m->type[c];
+    const int32_t *vi = m->idx + m->off[c];
+    const int nv = type;
+    r[0] = r[1] = r[2] = (type == 4) ? 0.25 : (type == 6 ? 1.0 / 3.0 : 0.5);
+    if (type == 6) r[2] = 0.5;
+    if (type == 5) r[2] = 0.2;
+    for (int it = 0; it < 60; ++it) {
+        double N[8], dN[8][3], x[3] = {0, 0, 0}, J[3][3] = {{0}};
+        shape_fn(type, r, N, dN);
+        for (int i = 0; i < nv; ++i) {
+            const double *X = m->X + 3 * (int64_t)vi[i];
+            for (int k = 0; k < 3; ++k) {
+                x[k] += N[i] * X[k];
+                for (int l = 0; l < 3; ++l) J[k][l] += X[k] * dN[i][l];
+            }
+        }
+        double F[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+        double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        if (!(fabs(det) > 0.0)) break;
+        double d[3];
+        for (int k = 0; k < 3; ++k) {
+            double M[3][3];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) M[a][b] = (b == k) ? F[a] : J[a][b];
+            d[k] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                    M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) / det;
+        }
+        for (int k = 0; k < 3; ++k) r[k] -= d[k];
+        if (fabs(d[0]) + fabs(d[1]) + fabs(d[2]) < 1e-15) break;
+        if (fabs(r[0]) + fabs(r[1]) + fabs(r[2]) > 1e6) break;   /* far outside: diverged */
+    }
+    /* a parametric point counts only if it maps back onto p (Newton converged) */
+    double N[8], dN[8][3], x[3] = {0, 0, 0}, ext = 0.0;
+    shape_fn(type, r, N, dN);
+    for (int i = 0; i < nv; ++i) {
+        const double *X = m->X + 3 * (int64_t)vi[i];
+        for (int k = 0; k < 3; ++k) {
+            x[k] += N[i] * X[k];
+            ext = fmax(ext, fabs(X[k] - m->X[3 * (int64_t)vi[0] + k]));
+        }
+    }
+    const double res = fabs(x[0] - p[0]) + fabs(x[1] - p[1]) + fabs(x[2] - p[2]);
+    if (!(res <= 1e-9 * ext)) return INFINITY;
+    return param_violation(type, r);
+}
+
+static void cell_value(const umesh *m, int64_t c, const double r[3], double v[3])
+{
+    const int type = m->type[c];
+    const int32_t *vi = m->idx + m->off[c];
+    double N[8], dN[8][3];
+    shape_fn(type, r, N, dN);
+    v[0] = v[1] = v[2] = 0.0;
+    for (int i = 0; i < type; ++i)
+        for (int k = 0; k < 3; ++k) v[k] += N[i] * m->V[3 * (int64_t)vi[i] + k];
+}
+
+/* Cell containing p, or -1; r receives its parametric coordinates.  Search
+ * order: the hint, the cells sharing a vertex with it, then every cell (any
+ * containing cell gives the same value on a conforming mesh). */
+static int64_t umesh_locate(const umesh *m, const double p[3], int64_t hint, double r[3])
+{
+    if (hint >= 0) {
+        if (cell_param(m, hint, p, r) <= m->tau) return hint;
+        for (int64_t k = m->off[hint]; k < m->off[hint + 1]; ++k) {
+            const int32_t v = m->idx[k];
+            for (int64_t j = m->vc_off[v]; j < m->vc_off[v + 1]; ++j)
+                if (cell_param(m, m->vc[j], p, r) <= m->tau) return m->vc[j];
+        }
+    }
+    for (int64_t c = 0; c < m->n_cells; ++c)
+        if (cell_param(m, c, p, r) <= m->tau) return c;
+    return -1;
+}
+
+/* vertex -> cells adjacency (CSR); the caller frees both arrays */
+static int build_adjacency(umesh *m, int64_t n_vertices)
+{
+    int64_t *cnt = (int64_t *)calloc((size_t)n_vertices + 1, sizeof(int64_t));
+    if (!cnt) return -1;
+    for (int64_t k = 0; k < m->off[m->n_cells]; ++k) cnt[m->idx[k] + 1] += 1;
+    for (int64_t v = 0; v < n_vertices; ++v) cnt[v + 1] += cnt[v];
+    int64_t *vc = (int64_t *)malloc(sizeof(int64_t) * (size_t)(cnt[n_vertices] + 1));
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_vertices + 1));
+    if (!vc || !pos) { free(cnt); free(vc); free(pos); return -1; }
+    memcpy(pos, cnt, sizeof(int64_t) * (size_t)(n_vertices + 1));
+    for (int64_t c = 0; c < m->n_cells; ++c)
+        for (int64_t k = m->off[c]; k < m->off[c + 1]; ++k) vc[pos[m->idx[k]]++] = c;
+    free(pos);
+    m->vc_off = cnt;
+    m->vc = vc;
+    return 0;
+}
+
+int or_umesh_sample(const double *X, const double *V, const int32_t *idx, const int64_t *off, const uint8_t *type,
+                    int64_t n_cells, double tau, const double *points, int64_t n, double *v, int64_t *cell)
+{
+    umesh m = {X, V, idx, off, type, n_cells, tau, NULL, NULL};
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double r[3];
+        int64_t c = umesh_locate(&m, points + 3 * i, -1, r);
+        cell[i] = c;
+        if (c >= 0) cell_value(&m, c, r, v + 3 * i);
+        else v[3 * i] = v[3 * i + 1] = v[3 * i + 2] = NAN;
+    }
+    return 0;
+}
+
+/* One RK4 step in world coordinates (Listing 1) on the unstructured field. */
+static int umesh_rk4(const umesh *m, const double p[3], double dt, double eps, int64_t *hint, double pn[3],
+                     double *margin)
+{
+    double r[3], v[3], k[4][3], q[3];
+    int64_t c = umesh_locate(m, p, *hint, r);
+    const int64_t c0 = c;
+    cell_value(m, c, r, v);
+    if (!all_finite(v)) return OR_NANFIELD;
+    double speed = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (speed < eps) { *margin = (eps - speed) / eps; return OR_STAGNANT; }
+    const double w[3] = {0.5, 0.5, 1.0};
+    for (int a = 0; a < 3; ++a) k[0][a] = dt * v[a];
+    for (int s = 1; s < 4; ++s) {
+        for (int a = 0; a < 3; ++a) q[a] = p[a] + w[s - 1] * k[s - 1][a];
+        c = umesh_locate(m, q, c, r);
+        if (c < 0) { double rr[3]; *margin = cell_param(m, c0, q, rr); return OR_EXIT; }
+        cell_value(m, c, r, v);
+        if (!all_finite(v)) return OR_NANFIELD;
+        for (int a = 0; a < 3; ++a) k[s][a] = dt * v[a];
+    }
+    for (int a = 0; a < 3; ++a) pn[a] = p[a] + (k[0][a] + 2.0 * k[1][a] + 2.0 * k[2][a] + k[3][a]) / 6.0;
+    c = umesh_locate(m, pn, c, r);
+    if (c < 0) { double rr[3]; *margin = cell_param(m, c0, pn, rr); return OR_EXIT; }
+    *hint = c;
+    return OR_ACTIVE;
+}
+
+/* Streamlines on an unstructured field.  seeds and verts in world
+ * coordinates (verts: n x (max_steps+1) x 3). */
+int or_umesh_trace(const double *X, const double *V, const int32_t *idx, const int64_t *off, const uint8_t *type,
+                   int64_t n_cells, int64_t n_vertices, double tau, const double *seeds, int64_t n, double dt,
+                   int64_t max_steps, double eps, double *verts, int32_t *len, uint8_t *status, double *margin,
+                   int nthreads)
+{
+    if (n < 0 || max_steps < 0 || n_cells < 0 || n_vertices < 0) return -1;
+    umesh m = {X, V, idx, off, type, n_cells, tau, NULL, NULL};
+    if (build_adjacency(&m, n_vertices)) return -1;
+    set_threads(nthreads);
+    int64_t stride = 3 * (max_steps + 1);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {seeds[3 * i], seeds[3 * i + 1], seeds[3 * i + 2]}, r[3];
+        double *out = verts + stride * i;
+        margin[i] = INFINITY;
+        int64_t hint = umesh_locate(&m, p, -1, r);
+        if (hint < 0) { len[i] = 0; status[i] = OR_OUT; continue; }
+        memcpy(out, p, sizeof p);
+        int64_t nv = 1;
+        for (int64_t s = 0;; ++s) {
+            if (s == max_steps) { status[i] = OR_MAXSTEPS; break; }
+            double pn[3];
+            int st = umesh_rk4(&m, p, dt, eps, &hint, pn, margin + i);
+            if (st != OR_ACTIVE) { status[i] = (uint8_t)st; break; }
+            memcpy(p, pn, sizeof p);
+            memcpy(out + 3 * nv, p, sizeof p);
+            ++nv;
+        }
+        len[i] = (int32_t)nv;
+    }
+    free((void *)m.vc_off);
+    free((void *)m.vc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Brick decomposition and the quantised field store.
  *
  * Reading (macrocells with a halo, Sec. 3.1.1): B bricks per axis; each owns

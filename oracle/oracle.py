@@ -61,6 +61,10 @@ def _load():
             lib.or_trace_streaklines.restype = ctypes.c_int
             lib.or_trace_pathlines.argtypes = [P, i64, P, P, P, d, P, i64, d, i64, d, P, P, P, P, ctypes.c_int]
             lib.or_trace_pathlines.restype = ctypes.c_int
+            lib.or_umesh_sample.argtypes = [P, P, P, P, P, i64, d, P, i64, P, P]
+            lib.or_umesh_sample.restype = ctypes.c_int
+            lib.or_umesh_trace.argtypes = [P, P, P, P, P, i64, i64, d, P, i64, d, i64, d, P, P, P, P, ctypes.c_int]
+            lib.or_umesh_trace.restype = ctypes.c_int
             lib.or_brick_cells.argtypes = [P, P, P]
             lib.or_brick_cells.restype = ctypes.c_int
             lib.or_owner_brick.argtypes = [P, P, P, P]
@@ -203,6 +207,48 @@ def trace_pathlines(slices, origin, spacing, slice_dt, seeds_world, dt, max_step
                                 _p(margin), int(nthreads))
     if rc:
         raise ValueError("or_trace_pathlines: bad arguments")
+    return Lines(verts, length, status, margin)
+
+
+def _umesh_args(mesh):
+    X = np.ascontiguousarray(mesh["vertices"], dtype=np.float64).reshape(-1, 3)
+    V = np.ascontiguousarray(mesh["velocity"], dtype=np.float64).reshape(-1, 3)
+    idx = np.ascontiguousarray(mesh["cell_vertices"], dtype=np.int32)
+    off = np.ascontiguousarray(mesh["cell_offsets"], dtype=np.int64)
+    typ = np.ascontiguousarray(mesh["cell_types"], dtype=np.uint8)
+    return X, V, idx, off, typ
+
+
+def umesh_sample(mesh, points, tau=1e-6, nthreads=0):
+    """Velocity (FP64) and containing cell (-1: none) at world points of an
+    unstructured mesh (dict of vertices, velocity, cell_vertices, cell_offsets,
+    cell_types); brute-force point location, see oracle.c."""
+    lib = _load()
+    X, V, idx, off, typ = _umesh_args(mesh)
+    P = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    v = np.zeros_like(P)
+    cell = np.zeros(len(P), dtype=np.int64)
+    if lib.or_umesh_sample(_p(X), _p(V), _p(idx), _p(off), _p(typ), len(typ), float(tau), _p(P), len(P), _p(v),
+                           _p(cell)):
+        raise ValueError("or_umesh_sample: bad arguments")
+    return v, cell
+
+
+def trace_umesh(mesh, seeds_world, dt, max_steps, eps=1e-6, tau=1e-6, nthreads=0) -> Lines:
+    """Streamlines on an unstructured mesh, FP64 (vertices in world coordinates)."""
+    lib = _load()
+    X, V, idx, off, typ = _umesh_args(mesh)
+    seeds = np.ascontiguousarray(np.asarray(seeds_world, dtype=np.float64).reshape(-1, 3))
+    n = seeds.shape[0]
+    verts = np.zeros((n, max_steps + 1, 3), dtype=np.float64)
+    length = np.zeros(n, dtype=np.int32)
+    status = np.zeros(n, dtype=np.uint8)
+    margin = np.zeros(n, dtype=np.float64)
+    rc = lib.or_umesh_trace(_p(X), _p(V), _p(idx), _p(off), _p(typ), len(typ), len(X), float(tau), _p(seeds), n,
+                            float(dt),
+                            int(max_steps), float(eps), _p(verts), _p(length), _p(status), _p(margin), int(nthreads))
+    if rc:
+        raise ValueError("or_umesh_trace: bad arguments")
     return Lines(verts, length, status, margin)
 
 

@@ -97,6 +97,11 @@ SIGNATURES = {
     "sg_tracer_total_steps": ([P, ctypes.POINTER(i64), P], i32),
     "sg_tracer_get_joined": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P], i32),
     "sg_seeds_rake": ([P, P, i64, P, P], i32),
+    "sg_umesh_required_bytes": ([i64, ctypes.POINTER(ctypes.c_size_t)], i32),
+    "sg_umesh_create": ([P, P, P, i64, P, P, P, i64, ctypes.c_float, P, ctypes.c_size_t, ctypes.POINTER(P)], i32),
+    "sg_umesh_destroy": ([P], i32),
+    "sg_umesh_sample": ([P, P, i64, P, P, P], i32),
+    "sg_umesh_trace": ([P, P, i64, ctypes.c_double, i32, ctypes.c_float, P, P, P, P, P], i32),
     "sg_tracer_pod_setup": ([P, P, i32, i32], i32),
     "sg_tracer_pod_begin": ([P, ctypes.POINTER(i64), P], i32),
     "sg_tracer_pod_round": ([P, ctypes.POINTER(i64), P, P], i32),

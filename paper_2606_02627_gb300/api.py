@@ -376,6 +376,67 @@ class Tracer:
             pass
 
 
+class UMesh:
+    """Unstructured field (tetrahedra, pyramids, prisms, hexahedra) with the
+    velocity at its vertices; a hierarchy for point location (sg_umesh_*)."""
+
+    def __init__(self, ctx: Context, mesh: dict, tau: float = 0.0):
+        self.ctx = ctx
+        X = np.ascontiguousarray(mesh["vertices"], dtype=np.float32)
+        V = np.ascontiguousarray(mesh["velocity"], dtype=np.float32)
+        idx = np.ascontiguousarray(mesh["cell_vertices"], dtype=np.int32)
+        off = np.ascontiguousarray(mesh["cell_offsets"], dtype=np.int64)
+        typ = np.ascontiguousarray(mesh["cell_types"], dtype=np.uint8)
+        self.n_cells = len(typ)
+        nbytes = ctypes.c_size_t()
+        call("sg_umesh_required_bytes", self.n_cells, ctypes.byref(nbytes))
+        self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=f"cuda:{ctx.device}")
+        h = ctypes.c_void_p()
+        call("sg_umesh_create", ctx.h, _ptr(X), _ptr(V), len(X), _ptr(idx), _ptr(off), _ptr(typ), self.n_cells,
+             float(tau), _ptr(self.workspace), nbytes.value, ctypes.byref(h))
+        self.h = h
+
+    def sample(self, points, stream=None):
+        """(velocity [n, 3] float32, cell [n] int64) at world points (device)."""
+        pts = torch.as_tensor(points, dtype=torch.float32).to(f"cuda:{self.ctx.device}").contiguous()
+        n = pts.shape[0]
+        v = torch.empty((max(n, 1), 3), dtype=torch.float32, device=pts.device)
+        c = torch.empty(max(n, 1), dtype=torch.int64, device=pts.device)
+        call("sg_umesh_sample", self.h, _ptr(pts), n, _ptr(v), _ptr(c), _stream(stream))
+        return v[:n], c[:n]
+
+    def trace(self, seeds, dt: float, max_steps: int, eps: float = 1e-6, stream=None) -> Lines:
+        """Streamlines from world seeds, compacted to CSR (device)."""
+        dev = f"cuda:{self.ctx.device}"
+        s = torch.as_tensor(seeds, dtype=torch.float32).to(dev).contiguous()
+        n = s.shape[0]
+        W = int(max_steps) + 1
+        slab = torch.empty((max(n, 1), W, 3), dtype=torch.float32, device=dev)
+        length = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        st = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+        mg = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+        call("sg_umesh_trace", self.h, _ptr(s), n, float(dt), int(max_steps), float(eps), _ptr(slab), _ptr(length),
+             _ptr(st), _ptr(mg), _stream(stream))
+        off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        call("sg_lines_compact_static", _ptr(slab), W, _ptr(length), n, _ptr(off), None, _stream(stream))
+        total = int(off[n].item()) if n else 0
+        vert = torch.empty((max(total, 1), 3), dtype=torch.float32, device=dev)
+        call("sg_lines_compact_static", _ptr(slab), W, _ptr(length), n, _ptr(off), _ptr(vert), _stream(stream))
+        src = torch.arange(n, dtype=torch.int32, device=dev)
+        return Lines(off, vert[:total], st[:n], mg[:n], src)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.lib().sg_umesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Continuous batching of streamline requests (sg_batch_*): requests join
     between runs and leave when their last line stops."""

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstreamgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "field.cu", "advect.cu", "queue.cu", "compact.cu", "streak.cu", "batch.cu", "seeds.cu", "pod.cu"]
+SOURCES = ["api.cu", "field.cu", "advect.cu", "queue.cu", "compact.cu", "streak.cu", "batch.cu", "seeds.cu", "pod.cu", "umesh.cu"]
 HEADERS = ["common.cuh", "tracer.cuh", "rk4.cuh"]
 
 

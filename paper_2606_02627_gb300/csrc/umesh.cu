@@ -1,0 +1,543 @@
+// Unstructured fields (the second field type of Sec. 3.3): a mesh of
+// tetrahedra, pyramids, prisms and hexahedra (VTK vertex orders) carrying the
+// velocity at its vertices, interpolated with each cell's isoparametric
+// shape functions; cells are located with a bounding volume hierarchy and a
+// point-in-cell test (the parametric solution of sum N_i(r) x_i = p, found by
+// Newton's method, inside the cell's reference domain within tau).
+//
+// Layout (caller's workspace): one 256-byte record per cell, the eight
+// vertex positions (float4, the cell type in the first w) and the eight
+// vertex velocities (float4), so that testing and interpolating a cell reads
+// one contiguous record; the cells are stored in the order of the BVH's
+// leaves, each leaf a contiguous range; BVH nodes are 32 bytes (box with the
+// child / range in the w words).  The hierarchy is built on the host at
+// creation (median split of the cell centroids along the widest axis, at
+// most 4 cells per leaf).
+//
+// Tracing: one thread per seed to termination (Listing 1's RK4 in world
+// coordinates, positions in FP64, samples in FP32 relative to the cell), the
+// cell of the previous sample tried first, then the BVH.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "rk4.cuh"
+
+namespace sg {
+
+struct __align__(16) UCell {
+    float4 x[8];                 // vertex positions; x[0].w holds the cell type (4, 5, 6, 8)
+    float4 v[8];                 // vertex velocities
+};
+
+struct __align__(16) UNode {
+    float4 lo;                   // w: leaf: first cell (int bits); inner: left child
+    float4 hi;                   // w: leaf: cell count (> 0); inner: -(right child) (int bits)
+};
+
+constexpr int UMESH_LEAF = 4;
+constexpr int UMESH_STACK = 64;
+constexpr int UMESH_NEWTON = 12;
+
+}  // namespace sg
+
+struct sg_umesh {
+    sg_context *ctx;
+    int64_t n_cells;
+    int64_t n_nodes;
+    float tau;
+    sg::UCell *cells;
+    sg::UNode *nodes;
+    int32_t *orig;               // original index of every stored cell
+    float lo[3], hi[3];          // bounds of the mesh
+};
+
+namespace sg {
+
+__device__ __forceinline__ void ushape(int type, float a, float b, float c, float N[8], float dN[8][3])
+{
+    if (type == 4) {
+        N[0] = 1.f - a - b - c; N[1] = a; N[2] = b; N[3] = c;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dN[i][0] = dN[i][1] = dN[i][2] = 0.f;
+        dN[0][0] = dN[0][1] = dN[0][2] = -1.f;
+        dN[1][0] = 1.f; dN[2][1] = 1.f; dN[3][2] = 1.f;
+    } else if (type == 5) {
+        N[0] = (1 - a) * (1 - b) * (1 - c); N[1] = a * (1 - b) * (1 - c);
+        N[2] = a * b * (1 - c); N[3] = (1 - a) * b * (1 - c); N[4] = c;
+        dN[0][0] = -(1 - b) * (1 - c); dN[0][1] = -(1 - a) * (1 - c); dN[0][2] = -(1 - a) * (1 - b);
+        dN[1][0] = (1 - b) * (1 - c);  dN[1][1] = -a * (1 - c);       dN[1][2] = -a * (1 - b);
+        dN[2][0] = b * (1 - c);        dN[2][1] = a * (1 - c);        dN[2][2] = -a * b;
+        dN[3][0] = -b * (1 - c);       dN[3][1] = (1 - a) * (1 - c);  dN[3][2] = -(1 - a) * b;
+        dN[4][0] = 0.f;                dN[4][1] = 0.f;                dN[4][2] = 1.f;
+    } else if (type == 6) {
+        N[0] = (1 - a - b) * (1 - c); N[1] = a * (1 - c); N[2] = b * (1 - c);
+        N[3] = (1 - a - b) * c;       N[4] = a * c;       N[5] = b * c;
+        dN[0][0] = -(1 - c); dN[0][1] = -(1 - c); dN[0][2] = -(1 - a - b);
+        dN[1][0] = (1 - c);  dN[1][1] = 0.f;      dN[1][2] = -a;
+        dN[2][0] = 0.f;      dN[2][1] = (1 - c);  dN[2][2] = -b;
+        dN[3][0] = -c;       dN[3][1] = -c;       dN[3][2] = (1 - a - b);
+        dN[4][0] = c;        dN[4][1] = 0.f;      dN[4][2] = a;
+        dN[5][0] = 0.f;      dN[5][1] = c;        dN[5][2] = b;
+    } else {
+        N[0] = (1 - a) * (1 - b) * (1 - c); N[1] = a * (1 - b) * (1 - c);
+        N[2] = a * b * (1 - c);             N[3] = (1 - a) * b * (1 - c);
+        N[4] = (1 - a) * (1 - b) * c;       N[5] = a * (1 - b) * c;
+        N[6] = a * b * c;                   N[7] = (1 - a) * b * c;
+        dN[0][0] = -(1 - b) * (1 - c); dN[0][1] = -(1 - a) * (1 - c); dN[0][2] = -(1 - a) * (1 - b);
+        dN[1][0] = (1 - b) * (1 - c);  dN[1][1] = -a * (1 - c);       dN[1][2] = -a * (1 - b);
+        dN[2][0] = b * (1 - c);        dN[2][1] = a * (1 - c);        dN[2][2] = -a * b;
+        dN[3][0] = -b * (1 - c);       dN[3][1] = (1 - a) * (1 - c);  dN[3][2] = -(1 - a) * b;
+        dN[4][0] = -(1 - b) * c;       dN[4][1] = -(1 - a) * c;       dN[4][2] = (1 - a) * (1 - b);
+        dN[5][0] = (1 - b) * c;        dN[5][1] = -a * c;             dN[5][2] = a * (1 - b);
+        dN[6][0] = b * c;              dN[6][1] = a * c;              dN[6][2] = a * b;
+        dN[7][0] = -b * c;             dN[7][1] = (1 - a) * c;        dN[7][2] = (1 - a) * b;
+    }
+}
+
+__device__ __forceinline__ float uviolation(int type, const float r[3])
+{
+    float v = fmaxf(-r[0], fmaxf(-r[1], -r[2]));
+    if (type == 4) v = fmaxf(v, r[0] + r[1] + r[2] - 1.f);
+    else if (type == 6) v = fmaxf(v, fmaxf(r[0] + r[1] - 1.f, r[2] - 1.f));
+    else v = fmaxf(v, fmaxf(r[0] - 1.f, fmaxf(r[1] - 1.f, r[2] - 1.f)));
+    return v;
+}
+
+// Parametric coordinates of p in the cell (Newton's method from its centre),
+// in coordinates relative to the cell's first vertex so that FP32 keeps its
+// precision relative to the cell's size; returns how far outside the
+// reference domain they lie (<= tau: inside).
+__device__ float ucell_param(const UCell &C, double3 pw, float r[3])
+{
+    const int type = __float_as_int(C.x[0].w);
+    const float4 X0 = C.x[0];
+    const float3 p = make_float3((float)(pw.x - (double)X0.x), (float)(pw.y - (double)X0.y),
+                                 (float)(pw.z - (double)X0.z));
+    r[0] = r[1] = r[2] = type == 4 ? 0.25f : (type == 6 ? (1.f / 3.f) : 0.5f);
+    if (type == 6) r[2] = 0.5f;
+    if (type == 5) r[2] = 0.2f;
+    for (int it = 0; it < UMESH_NEWTON; ++it) {
+        float N[8], dN[8][3];
+        ushape(type, r[0], r[1], r[2], N, dN);
+        float x0 = -p.x, x1 = -p.y, x2 = -p.z;
+        float J[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        for (int i = 0; i < type; ++i) {
+            const float4 Xw = C.x[i];
+            const float3 X = make_float3(Xw.x - X0.x, Xw.y - X0.y, Xw.z - X0.z);
+            x0 = fmaf(N[i], X.x, x0);
+            x1 = fmaf(N[i], X.y, x1);
+            x2 = fmaf(N[i], X.z, x2);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                J[0][l] = fmaf(X.x, dN[i][l], J[0][l]);
+                J[1][l] = fmaf(X.y, dN[i][l], J[1][l]);
+                J[2][l] = fmaf(X.z, dN[i][l], J[2][l]);
+            }
+        }
+        const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        const float det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        if (!(fabsf(det) > 0.f)) break;
+        const float inv = 1.f / det;
+        // d = J^-1 F (adjugate)
+        const float d0 = (c00 * x0 + (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * x1 + (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * x2) * inv;
+        const float d1 = (c01 * x0 + (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * x1 + (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * x2) * inv;
+        const float d2 = (c02 * x0 + (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * x1 + (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * x2) * inv;
+        r[0] -= d0;
+        r[1] -= d1;
+        r[2] -= d2;
+        if (fabsf(d0) + fabsf(d1) + fabsf(d2) < 1e-7f) break;
+        if (fabsf(r[0]) + fabsf(r[1]) + fabsf(r[2]) > 1e6f) break;
+    }
+    // a parametric point counts only if it maps back onto p (Newton converged)
+    float N[8], dN[8][3];
+    ushape(type, r[0], r[1], r[2], N, dN);
+    float x0 = -p.x, x1 = -p.y, x2 = -p.z, ext = 0.f;
+    for (int i = 0; i < type; ++i) {
+        const float4 Xw = C.x[i];
+        const float3 X = make_float3(Xw.x - X0.x, Xw.y - X0.y, Xw.z - X0.z);
+        x0 = fmaf(N[i], X.x, x0);
+        x1 = fmaf(N[i], X.y, x1);
+        x2 = fmaf(N[i], X.z, x2);
+        ext = fmaxf(ext, fmaxf(fabsf(X.x), fmaxf(fabsf(X.y), fabsf(X.z))));
+    }
+    if (!(fabsf(x0) + fabsf(x1) + fabsf(x2) <= 1e-4f * ext)) return INFINITY;
+    return uviolation(type, r);
+}
+
+__device__ float3 ucell_value(const UCell &C, const float r[3])
+{
+    const int type = __float_as_int(C.x[0].w);
+    float N[8], dN[8][3];
+    ushape(type, r[0], r[1], r[2], N, dN);
+    float3 v = make_float3(0.f, 0.f, 0.f);
+    for (int i = 0; i < type; ++i) {
+        const float4 V = C.v[i];
+        v.x = fmaf(N[i], V.x, v.x);
+        v.y = fmaf(N[i], V.y, v.y);
+        v.z = fmaf(N[i], V.z, v.z);
+    }
+    return v;
+}
+
+struct UMeshView {
+    const UCell *cells;
+    const UNode *nodes;
+    long long n_cells;
+    float tau;
+};
+
+// The stored cell containing p (hint first, then the hierarchy), or -1.
+__device__ long long ulocate(const UMeshView &M, double3 pw, long long hint, float r[3])
+{
+    if (hint >= 0 && ucell_param(M.cells[hint], pw, r) <= M.tau) return hint;
+    const float3 p = make_float3((float)pw.x, (float)pw.y, (float)pw.z);
+    if (M.n_cells == 0) return -1;
+    int stack[UMESH_STACK];
+    int top = 0;
+    stack[top++] = 0;
+    while (top > 0) {
+        const UNode n = M.nodes[stack[--top]];
+        if (p.x < n.lo.x || p.y < n.lo.y || p.z < n.lo.z || p.x > n.hi.x || p.y > n.hi.y || p.z > n.hi.z) continue;
+        const int a = __float_as_int(n.lo.w), b = __float_as_int(n.hi.w);
+        if (b > 0) {
+            for (int k = 0; k < b; ++k)
+                if (ucell_param(M.cells[a + k], pw, r) <= M.tau) return a + k;
+        } else if (top + 2 <= UMESH_STACK) {
+            stack[top++] = -b;
+            stack[top++] = a;
+        }
+    }
+    return -1;
+}
+
+__global__ void umesh_sample_kernel(UMeshView M, const int32_t *orig, const float *pts, long long n, float *vel,
+                                    int64_t *cell)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double3 p = make_double3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        float r[3];
+        const long long c = ulocate(M, p, -1, r);
+        float3 v = make_float3(NAN, NAN, NAN);
+        if (c >= 0) v = ucell_value(M.cells[c], r);
+        vel[3 * i] = v.x;
+        vel[3 * i + 1] = v.y;
+        vel[3 * i + 2] = v.z;
+        if (cell) cell[i] = c >= 0 ? orig[c] : -1;
+    }
+}
+
+struct UTraceArgs {
+    const float *seeds;
+    long long n;
+    float dt;
+    float eps;
+    uint32_t max_steps;
+    long long W;
+    float *slab;
+    uint32_t *len;
+    uint8_t *status;
+    float *margin;
+    float tie_cells, tie_eps_rel;
+};
+
+// One RK4 step (Listing 1) in world coordinates; returns the status
+// (SG_LINE_ACTIVE on success with pn set).  Positions are kept in FP64 (a
+// handful of additions per step); the samples are FP32.
+__device__ int urk4(const UMeshView &M, double3 p, float dt, float eps, long long &hint, double3 &pn, float &margin)
+{
+    float r[3];
+    long long c = ulocate(M, p, hint, r);
+    const long long c0 = c;
+    float3 v = ucell_value(M.cells[c], r);
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+    if (sp < eps) {
+        margin = (eps - sp) / eps;
+        return SG_LINE_STAGNANT;
+    }
+    float3 k[4];
+    k[0] = make_float3(dt * v.x, dt * v.y, dt * v.z);
+    const float w[3] = {0.5f, 0.5f, 1.0f};
+    for (int s = 1; s < 4; ++s) {
+        const double3 q = make_double3(p.x + (double)(w[s - 1] * k[s - 1].x), p.y + (double)(w[s - 1] * k[s - 1].y),
+                                       p.z + (double)(w[s - 1] * k[s - 1].z));
+        c = ulocate(M, q, c, r);
+        if (c < 0) {
+            float rr[3];
+            margin = ucell_param(M.cells[c0], q, rr);
+            return SG_LINE_EXIT;
+        }
+        v = ucell_value(M.cells[c], r);
+        if (bad3(v)) return SG_LINE_NANFIELD;
+        k[s] = make_float3(dt * v.x, dt * v.y, dt * v.z);
+    }
+    pn = make_double3(p.x + (double)((k[0].x + 2.f * k[1].x + 2.f * k[2].x + k[3].x) * (1.f / 6.f)),
+                      p.y + (double)((k[0].y + 2.f * k[1].y + 2.f * k[2].y + k[3].y) * (1.f / 6.f)),
+                      p.z + (double)((k[0].z + 2.f * k[1].z + 2.f * k[2].z + k[3].z) * (1.f / 6.f)));
+    c = ulocate(M, pn, c, r);
+    if (c < 0) {
+        float rr[3];
+        margin = ucell_param(M.cells[c0], pn, rr);
+        return SG_LINE_EXIT;
+    }
+    hint = c;
+    return SG_LINE_ACTIVE;
+}
+
+__global__ void __launch_bounds__(256) umesh_trace_kernel(UMeshView M, UTraceArgs A)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += (long long)gridDim.x * blockDim.x) {
+        double3 p = make_double3(A.seeds[3 * i], A.seeds[3 * i + 1], A.seeds[3 * i + 2]);
+        float r[3];
+        long long hint = ulocate(M, p, -1, r);
+        float margin = INFINITY;
+        A.margin[i] = INFINITY;
+        if (hint < 0) {
+            A.len[i] = 0;
+            A.status[i] = SG_LINE_OUT;
+            continue;
+        }
+        float *out = A.slab + i * A.W * 3;
+        out[0] = A.seeds[3 * i];
+        out[1] = A.seeds[3 * i + 1];
+        out[2] = A.seeds[3 * i + 2];
+        uint32_t step = 0;
+        int st = SG_LINE_MAXSTEPS;
+        while (step < A.max_steps) {
+            double3 pn;
+            const int s = urk4(M, p, A.dt, A.eps, hint, pn, margin);
+            if (s != SG_LINE_ACTIVE) {
+                st = s;
+                break;
+            }
+            p = pn;
+            ++step;
+            st_na(out + 3ll * step, (float)p.x);
+            st_na(out + 3ll * step + 1, (float)p.y);
+            st_na(out + 3ll * step + 2, (float)p.z);
+        }
+        A.len[i] = step + 1;
+        A.status[i] = stop_code_t(st, margin, A.tie_cells, A.tie_eps_rel);
+        A.margin[i] = margin;
+    }
+}
+
+// ------------------------------------------------------------------ host: hierarchy build
+
+struct BuildItem {
+    int node, first, count;
+};
+
+static int64_t max_nodes(int64_t n_cells) { return n_cells > 0 ? 2 * n_cells : 1; }
+
+}  // namespace sg
+
+using namespace sg;
+
+static size_t umesh_bytes(int64_t n_cells)
+{
+    return align_up(sizeof(UCell) * (size_t)n_cells, 256) + align_up(sizeof(UNode) * (size_t)max_nodes(n_cells), 256) +
+           align_up(sizeof(int32_t) * (size_t)n_cells, 256);
+}
+
+extern "C" sg_status sg_umesh_required_bytes(int64_t n_cells, size_t *bytes)
+{
+    SG_CHECK(bytes && n_cells >= 0 && n_cells < (1ll << 30), SG_ERR_INVALID_ARG, "bad cell count");
+    *bytes = umesh_bytes(n_cells);
+    return SG_OK;
+}
+
+extern "C" sg_status sg_umesh_create(sg_context *ctx, const float *vertices, const float *velocity, int64_t n_vertices,
+                                     const int32_t *cell_vertices, const int64_t *cell_offsets, const uint8_t *cell_types,
+                                     int64_t n_cells, float tau, void *workspace, size_t bytes, sg_umesh **out)
+{
+    SG_CHECK(ctx && out && n_vertices >= 0 && n_cells >= 0 && n_cells < (1ll << 30), SG_ERR_INVALID_ARG,
+             "bad arguments");
+    SG_CHECK(n_cells == 0 || (vertices && velocity && cell_vertices && cell_offsets && cell_types), SG_ERR_INVALID_ARG,
+             "NULL mesh array");
+    SG_CHECK(workspace && ((uintptr_t)workspace & 255) == 0 && bytes >= umesh_bytes(n_cells), SG_ERR_OOM,
+             "workspace of %zu bytes (256-byte aligned) needed", umesh_bytes(n_cells));
+    SG_CHECK(pointer_kind(workspace) == PTR_DEVICE, SG_ERR_INVALID_ARG, "workspace must be device memory");
+    SG_CHECK(tau >= 0.f && tau < 0.5f, SG_ERR_INVALID_ARG, "tau must be in [0, 0.5)");
+    const float tol = tau > 0.f ? tau : 1e-5f;
+    // cell records and boxes
+    std::vector<UCell> rec((size_t)n_cells);
+    std::vector<float> box((size_t)n_cells * 6), cen((size_t)n_cells * 3);
+    float glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t c = 0; c < n_cells; ++c) {
+        const int type = cell_types[c];
+        SG_CHECK(type == 4 || type == 5 || type == 6 || type == 8, SG_ERR_INVALID_ARG, "cell %lld: type %d",
+                 (long long)c, type);
+        SG_CHECK(cell_offsets[c + 1] - cell_offsets[c] == type, SG_ERR_INVALID_ARG,
+                 "cell %lld: %lld vertices for type %d", (long long)c,
+                 (long long)(cell_offsets[c + 1] - cell_offsets[c]), type);
+        UCell &u = rec[(size_t)c];
+        memset(&u, 0, sizeof u);
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int i = 0; i < type; ++i) {
+            const int64_t vi = cell_vertices[cell_offsets[c] + i];
+            SG_CHECK(vi >= 0 && vi < n_vertices, SG_ERR_INVALID_ARG, "cell %lld: vertex %lld out of range",
+                     (long long)c, (long long)vi);
+            u.x[i] = make_float4(vertices[3 * vi], vertices[3 * vi + 1], vertices[3 * vi + 2], 0.f);
+            u.v[i] = make_float4(velocity[3 * vi], velocity[3 * vi + 1], velocity[3 * vi + 2], 0.f);
+            const float *X = vertices + 3 * vi;
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], X[a]);
+                hi[a] = std::max(hi[a], X[a]);
+            }
+        }
+        int tbits = type;
+        memcpy(&u.x[0].w, &tbits, 4);
+        for (int a = 0; a < 3; ++a) {
+            // boxes grow by the containment tolerance (relative to the cell)
+            const float pad = (hi[a] - lo[a]) * tol + 1e-30f;
+            box[6 * c + a] = lo[a] - pad;
+            box[6 * c + 3 + a] = hi[a] + pad;
+            cen[3 * c + a] = 0.5f * (lo[a] + hi[a]);
+            glo[a] = std::min(glo[a], lo[a]);
+            ghi[a] = std::max(ghi[a], hi[a]);
+        }
+    }
+    // hierarchy: median split of the centroids along the widest axis
+    std::vector<int32_t> order((size_t)n_cells);
+    for (int64_t c = 0; c < n_cells; ++c) order[(size_t)c] = (int32_t)c;
+    std::vector<UNode> nodes;
+    nodes.reserve((size_t)max_nodes(n_cells));
+    if (n_cells > 0) {
+        nodes.push_back(UNode());
+        std::vector<BuildItem> todo{{0, 0, (int)n_cells}};
+        while (!todo.empty()) {
+            const BuildItem it = todo.back();
+            todo.pop_back();
+            float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int k = it.first; k < it.first + it.count; ++k) {
+                const int c = order[(size_t)k];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = std::min(lo[a], box[6 * c + a]);
+                    hi[a] = std::max(hi[a], box[6 * c + 3 + a]);
+                    clo[a] = std::min(clo[a], cen[3 * c + a]);
+                    chi[a] = std::max(chi[a], cen[3 * c + a]);
+                }
+            }
+            UNode &nd = nodes[(size_t)it.node];
+            nd.lo = make_float4(lo[0], lo[1], lo[2], 0.f);
+            nd.hi = make_float4(hi[0], hi[1], hi[2], 0.f);
+            if (it.count <= UMESH_LEAF) {
+                int a = it.first, b = it.count;
+                memcpy(&nd.lo.w, &a, 4);
+                memcpy(&nd.hi.w, &b, 4);
+                continue;
+            }
+            int ax = 0;
+            for (int a = 1; a < 3; ++a)
+                if (chi[a] - clo[a] > chi[ax] - clo[ax]) ax = a;
+            const int mid = it.first + it.count / 2;
+            std::nth_element(order.begin() + it.first, order.begin() + mid, order.begin() + it.first + it.count,
+                             [&](int32_t p, int32_t q) { return cen[3 * p + ax] < cen[3 * q + ax]; });
+            const int left = (int)nodes.size(), right = left + 1;
+            nodes.push_back(UNode());
+            nodes.push_back(UNode());
+            UNode &nd2 = nodes[(size_t)it.node];        // the push_backs may have moved it
+            int l = left, r = -right;
+            memcpy(&nd2.lo.w, &l, 4);
+            memcpy(&nd2.hi.w, &r, 4);
+            todo.push_back({right, mid, it.first + it.count - mid});
+            todo.push_back({left, it.first, mid - it.first});
+        }
+    }
+    std::vector<UCell> sorted((size_t)n_cells);
+    for (int64_t k = 0; k < n_cells; ++k) sorted[(size_t)k] = rec[(size_t)order[(size_t)k]];
+    SG_CUDA(cudaSetDevice(ctx->device));
+    Carve cv{(char *)workspace, 0, 0};
+    UCell *dcells = (UCell *)cv.take(sizeof(UCell) * (size_t)n_cells);
+    UNode *dnodes = (UNode *)cv.take(sizeof(UNode) * (size_t)max_nodes(n_cells));
+    int32_t *dorig = (int32_t *)cv.take(sizeof(int32_t) * (size_t)n_cells);
+    if (n_cells > 0) {
+        SG_CUDA(cudaMemcpy(dcells, sorted.data(), sizeof(UCell) * (size_t)n_cells, cudaMemcpyHostToDevice));
+        SG_CUDA(cudaMemcpy(dnodes, nodes.data(), sizeof(UNode) * nodes.size(), cudaMemcpyHostToDevice));
+        SG_CUDA(cudaMemcpy(dorig, order.data(), sizeof(int32_t) * (size_t)n_cells, cudaMemcpyHostToDevice));
+    }
+    sg_umesh *m = new sg_umesh;
+    m->ctx = ctx;
+    m->n_cells = n_cells;
+    m->n_nodes = (int64_t)nodes.size();
+    m->tau = tol;
+    m->cells = dcells;
+    m->nodes = dnodes;
+    m->orig = dorig;
+    for (int a = 0; a < 3; ++a) {
+        m->lo[a] = glo[a];
+        m->hi[a] = ghi[a];
+    }
+    *out = m;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_umesh_destroy(sg_umesh *m)
+{
+    delete m;
+    return SG_OK;
+}
+
+static UMeshView view_of(const sg_umesh *m)
+{
+    UMeshView M;
+    M.cells = m->cells;
+    M.nodes = m->nodes;
+    M.n_cells = m->n_cells;
+    M.tau = m->tau;
+    return M;
+}
+
+extern "C" sg_status sg_umesh_sample(sg_umesh *m, const float *points, int64_t n, float *velocity, int64_t *cell,
+                                     void *stream)
+{
+    SG_CHECK(m && n >= 0 && (n == 0 || (points && velocity)), SG_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return SG_OK;
+    SG_CHECK(pointer_kind(points) == PTR_DEVICE && pointer_kind(velocity) == PTR_DEVICE &&
+                 (!cell || pointer_kind(cell) == PTR_DEVICE),
+             SG_ERR_INVALID_ARG, "points, velocity and cell must be device memory");
+    SG_CUDA(cudaSetDevice(m->ctx->device));
+    const long long g = (n + 255) / 256;
+    umesh_sample_kernel<<<(unsigned)(g < 65535 ? g : 65535), 256, 0, (cudaStream_t)stream>>>(view_of(m), m->orig,
+                                                                                          points, n, velocity, cell);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
+extern "C" sg_status sg_umesh_trace(sg_umesh *m, const float *seeds, int64_t n, double dt, int32_t max_steps, float eps,
+                                    float *slab, uint32_t *length, uint8_t *status, float *margin, void *stream)
+{
+    SG_CHECK(m && n >= 0 && max_steps >= 0 && max_steps < (1 << 27), SG_ERR_INVALID_ARG, "bad arguments");
+    SG_CHECK(dt > 0.0 && dt < 1e30 && eps >= 0.f, SG_ERR_INVALID_ARG, "bad dt or eps");
+    if (n == 0) return SG_OK;
+    for (const void *p : {(const void *)seeds, (const void *)slab, (const void *)length, (const void *)status,
+                          (const void *)margin})
+        SG_CHECK(p && pointer_kind(p) == PTR_DEVICE, SG_ERR_INVALID_ARG, "trace buffers must be device memory");
+    SG_CUDA(cudaSetDevice(m->ctx->device));
+    UTraceArgs A;
+    A.seeds = seeds;
+    A.n = n;
+    A.dt = (float)dt;
+    A.eps = eps;
+    A.max_steps = (uint32_t)max_steps;
+    A.W = (long long)max_steps + 1;
+    A.slab = slab;
+    A.len = length;
+    A.status = status;
+    A.margin = margin;
+    A.tie_cells = 1e-3f;
+    A.tie_eps_rel = 1e-3f;
+    long long g = (n + 255) / 256;
+    const long long cap = (long long)m->ctx->sm_count * 8;
+    if (g > cap) g = cap;
+    umesh_trace_kernel<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(view_of(m), A);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}

@@ -285,3 +285,63 @@ def max_speed_cells(field: np.ndarray, spacing) -> float:
     """max over samples of |v / spacing| (cells per unit time), FP64 on the host."""
     f = np.asarray(field, dtype=np.float64).reshape(-1, 3) / np.asarray(spacing, dtype=np.float64)
     return float(np.sqrt((f * f).sum(axis=1)).max())
+
+
+# ---------------------------------------------------------------- unstructured meshes
+
+# VTK cell types by vertex count: tetrahedron 4, pyramid 5, wedge (prism) 6, hexahedron 8
+TET, PYRAMID, PRISM, HEX = 4, 5, 6, 8
+
+# local corner numbering of a grid cell: corner k at (k & 1, k >> 1 & 1, k >> 2)
+_HEX_ORDER = (0, 1, 3, 2, 4, 5, 7, 6)          # VTK hexahedron order of those corners
+# six tetrahedra around the main diagonal (corners 0 and 7), the same in every cell
+_TETS = ((0, 1, 3, 7), (0, 3, 2, 7), (0, 2, 6, 7), (0, 6, 4, 7), (0, 4, 5, 7), (0, 5, 1, 7))
+# two wedges: bottom triangles (0,1,3) and (0,3,2), extruded in z
+_PRISMS = ((0, 1, 3, 4, 5, 7), (0, 3, 2, 4, 7, 6))
+# six faces as (VTK-ordered quad) bases of pyramids with apex at the centre
+_FACES = ((0, 2, 3, 1), (4, 5, 7, 6), (0, 1, 5, 4), (2, 6, 7, 3), (0, 4, 6, 2), (1, 3, 7, 5))
+
+
+def grid_mesh(grid: Grid, field: np.ndarray, kind: str = "hex", jitter: float = 0.0, seed: int = 0) -> dict:
+    """The cells of a structured grid as an unstructured mesh: each cell as one
+    hexahedron, six tetrahedra, two prisms or six pyramids (apex at the cell
+    centre, an extra vertex whose velocity is the mean of the eight corners).
+    jitter moves every interior vertex by up to jitter cells per axis
+    (uniform, SplitMix64 stream 30); the velocity stays at the vertices."""
+    nx, ny, nz = grid.dims
+    org = np.asarray(grid.origin, dtype=np.float64)
+    sp = np.asarray(grid.spacing, dtype=np.float64)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    X = org + sp * np.stack([i, j, k], -1).reshape(-1, 3).astype(np.float64)
+    V = np.asarray(field, dtype=np.float64).reshape(-1, 3).copy()
+    if jitter > 0.0:
+        u = uniform(seed, 30, X.size).reshape(-1, 3) * 2.0 - 1.0
+        inner = ((i > 0) & (i < nx - 1) & (j > 0) & (j < ny - 1) & (k > 0) & (k < nz - 1)).reshape(-1)
+        X[inner] += (jitter * sp) * u[inner]
+    ci, cj, ck = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), np.arange(nz - 1), indexing="ij")
+    base = ((ck * ny + cj) * nx + ci).reshape(-1)
+    corner_off = np.array([((c >> 2) * ny + ((c >> 1) & 1)) * nx + (c & 1) for c in range(8)])
+    corners = base[:, None] + corner_off[None, :]          # [n_cells, 8] in local corner numbering
+    if kind == "hex":
+        cells = corners[:, list(_HEX_ORDER)]
+        types = np.full(len(cells), HEX, np.uint8)
+    elif kind == "tet":
+        cells = np.concatenate([corners[:, list(t)] for t in _TETS])
+        types = np.full(len(cells), TET, np.uint8)
+    elif kind == "prism":
+        cells = np.concatenate([corners[:, list(p)] for p in _PRISMS])
+        types = np.full(len(cells), PRISM, np.uint8)
+    elif kind == "pyramid":
+        n0 = len(X)
+        centre = X[corners].mean(axis=1)
+        X = np.concatenate([X, centre])
+        V = np.concatenate([V, V[corners].mean(axis=1)])
+        apex = n0 + np.arange(len(corners))
+        cells = np.concatenate([np.concatenate([corners[:, list(f)], apex[:, None]], 1) for f in _FACES])
+        types = np.full(len(cells), PYRAMID, np.uint8)
+    else:
+        raise ValueError(kind)
+    nv = types.astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(nv)])
+    return {"vertices": X, "velocity": V, "cell_vertices": cells.reshape(-1).astype(np.int32), "cell_offsets": off,
+            "cell_types": types}

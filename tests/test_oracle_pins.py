@@ -564,3 +564,56 @@ def test_pathlines_exact_for_linear_in_time_flow():
 
     for j in range(13):
         np.testing.assert_allclose(P.line(0)[j], x0[0] + X(j * dt), atol=1e-12)
+
+
+# ---------------------------------------------------------------- unstructured fields
+
+_A = np.array([[0.3, -0.2, 0.1], [0.05, 0.4, -0.3], [0.2, 0.1, -0.1]])
+_B = np.array([0.5, -0.25, 0.75])
+
+
+@pytest.mark.parametrize("kind", ["hex", "tet", "prism", "pyramid"])
+def test_umesh_cells_reproduce_linear_fields(kind):
+    # every isoparametric cell reproduces a field linear in x exactly, whatever
+    # the shape of the (jittered) cell: a check of point location, Newton's
+    # inversion and the shape functions together
+    g = inputs.Grid((6, 5, 4), (1.0, -2.0, 0.5), (0.5, 0.75, 1.0))
+    m = inputs.grid_mesh(g, np.zeros((4, 5, 6, 3)), kind=kind, jitter=0.25, seed=7)
+    m["velocity"] = m["vertices"] @ _A.T + _B
+    lo = np.asarray(g.origin) + 0.01
+    hi = np.asarray(g.origin) + np.asarray(g.spacing) * (np.asarray(g.dims) - 1) - 0.01
+    pts = lo + (hi - lo) * inputs.uniform(5, 1, 3000).reshape(-1, 3)
+    v, cell = oracle.umesh_sample(m, pts)
+    assert (cell >= 0).all()
+    np.testing.assert_allclose(v, pts @ _A.T + _B, atol=1e-12)
+    out = np.array([[lo[0] - 0.5, lo[1] + 1, lo[2] + 1], [hi[0] + 0.3, lo[1], lo[2]], [lo[0], lo[1], hi[2] + 2.0]])
+    _, c = oracle.umesh_sample(m, out)
+    assert (c == -1).all()
+
+
+def test_umesh_hexes_of_a_grid_trace_the_structured_lines():
+    # undistorted hexahedra of a grid interpolate trilinearly in the grid's
+    # fractions: the unstructured field is the structured one
+    g = inputs.Grid((13, 11, 12), (0.5, -1.0, 2.0), (0.5, 0.25, 0.75))
+    F = inputs.turbulence_field(g, inputs.turbulence_modes(8, n_modes=24, kmax=2)).numpy()
+    m = inputs.grid_mesh(g, F, kind="hex")
+    seeds = inputs.uniform_seeds(g, 60, 8)
+    dt = 0.4 / oracle.max_speed(F, g.spacing)
+    L = oracle.trace_streamlines(F, g.origin, g.spacing, seeds, dt, 80)
+    U = oracle.trace_umesh(m, seeds, dt, 80)
+    org, sp = np.asarray(g.origin), np.asarray(g.spacing)
+    for i in range(len(seeds)):
+        if L.status[i] == oracle.EXIT and abs(L.length[i] - U.length[i]) <= 1:
+            continue                                     # a stage point on the boundary face
+        assert L.length[i] == U.length[i] and L.status[i] == U.status[i]
+        np.testing.assert_allclose(U.line(i), org + sp * L.line(i), atol=1e-9)
+
+
+def test_umesh_uniform_flow_exact_line_and_exit():
+    g = inputs.Grid((9, 9, 9), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    m = inputs.grid_mesh(g, inputs.uniform_field(g, (0.25, 0.0, 0.0)), kind="tet", jitter=0.2, seed=2)
+    seed = np.array([[1.0, 4.3, 3.7]])
+    U = oracle.trace_umesh(m, seed, 1.0, 100)
+    # p_n = 1 + n/4 along x; the step from x = 8 has its first stage point at 8.125
+    assert U.status[0] == oracle.EXIT and U.length[0] == 29
+    np.testing.assert_allclose(U.line(0)[:, 0], 1.0 + 0.25 * np.arange(29), atol=1e-12)
