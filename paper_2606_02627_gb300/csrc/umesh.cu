@@ -110,15 +110,19 @@ __device__ __forceinline__ float uviolation(int type, const float r[3])
 // in coordinates relative to the cell's first vertex so that FP32 keeps its
 // precision relative to the cell's size; returns how far outside the
 // reference domain they lie (<= tau: inside).
-__device__ float ucell_param(const UCell &C, double3 pw, float r[3])
+// warm: r already holds a guess (the previous sample's coordinates in this
+// cell), else Newton starts from the cell's centre.
+__device__ float ucell_param(const UCell &C, double3 pw, float r[3], bool warm = false)
 {
     const int type = __float_as_int(C.x[0].w);
     const float4 X0 = C.x[0];
     const float3 p = make_float3((float)(pw.x - (double)X0.x), (float)(pw.y - (double)X0.y),
                                  (float)(pw.z - (double)X0.z));
-    r[0] = r[1] = r[2] = type == 4 ? 0.25f : (type == 6 ? (1.f / 3.f) : 0.5f);
-    if (type == 6) r[2] = 0.5f;
-    if (type == 5) r[2] = 0.2f;
+    if (!warm) {
+        r[0] = r[1] = r[2] = type == 4 ? 0.25f : (type == 6 ? (1.f / 3.f) : 0.5f);
+        if (type == 6) r[2] = 0.5f;
+        if (type == 5) r[2] = 0.2f;
+    }
     for (int it = 0; it < UMESH_NEWTON; ++it) {
         float N[8], dN[8][3];
         ushape(type, r[0], r[1], r[2], N, dN);
@@ -191,10 +195,12 @@ struct UMeshView {
     float tau;
 };
 
-// The stored cell containing p (hint first, then the hierarchy), or -1.
-__device__ long long ulocate(const UMeshView &M, double3 pw, long long hint, float r[3])
+// The stored cell containing p (hint first, then the hierarchy), or -1.  r
+// holds the parametric coordinates of the previous sample in the hint cell
+// (the warm start) and receives those of p.
+__device__ long long ulocate(const UMeshView &M, double3 pw, long long hint, float r[3], bool warm = false)
 {
-    if (hint >= 0 && ucell_param(M.cells[hint], pw, r) <= M.tau) return hint;
+    if (hint >= 0 && ucell_param(M.cells[hint], pw, r, warm) <= M.tau) return hint;
     const float3 p = make_float3((float)pw.x, (float)pw.y, (float)pw.z);
     if (M.n_cells == 0) return -1;
     int stack[UMESH_STACK];
@@ -248,11 +254,16 @@ struct UTraceArgs {
 // One RK4 step (Listing 1) in world coordinates; returns the status
 // (SG_LINE_ACTIVE on success with pn set).  Positions are kept in FP64 (a
 // handful of additions per step); the samples are FP32.
-__device__ int urk4(const UMeshView &M, double3 p, float dt, float eps, long long &hint, double3 &pn, float &margin)
+__device__ int urk4(const UMeshView &M, double3 p, float dt, float eps, long long &hint, float rp[3], double3 &pn,
+                    float &margin)
 {
-    float r[3];
-    long long c = ulocate(M, p, hint, r);
+    // rp: P0's coordinates in the hint cell (from the previous step's last locate)
+    float r[3] = {rp[0], rp[1], rp[2]}, r0[3];
+    long long c = ulocate(M, p, hint, r, true);
     const long long c0 = c;
+    r0[0] = r[0];
+    r0[1] = r[1];
+    r0[2] = r[2];
     float3 v = ucell_value(M.cells[c], r);
     if (bad3(v)) return SG_LINE_NANFIELD;
     const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
@@ -266,26 +277,36 @@ __device__ int urk4(const UMeshView &M, double3 p, float dt, float eps, long lon
     for (int s = 1; s < 4; ++s) {
         const double3 q = make_double3(p.x + (double)(w[s - 1] * k[s - 1].x), p.y + (double)(w[s - 1] * k[s - 1].y),
                                        p.z + (double)(w[s - 1] * k[s - 1].z));
-        c = ulocate(M, q, c, r);
-        if (c < 0) {
-            float rr[3];
-            margin = ucell_param(M.cells[c0], q, rr);
+        // stage points lie near P0: start from P0's coordinates in its cell
+        long long cs = c0;
+        float rs[3] = {r0[0], r0[1], r0[2]};
+        cs = ulocate(M, q, cs, rs, true);
+        if (cs < 0) {
+            float rr[3] = {r0[0], r0[1], r0[2]};
+            margin = ucell_param(M.cells[c0], q, rr, true);
             return SG_LINE_EXIT;
         }
-        v = ucell_value(M.cells[c], r);
+        c = cs;
+        v = ucell_value(M.cells[cs], rs);
         if (bad3(v)) return SG_LINE_NANFIELD;
         k[s] = make_float3(dt * v.x, dt * v.y, dt * v.z);
     }
     pn = make_double3(p.x + (double)((k[0].x + 2.f * k[1].x + 2.f * k[2].x + k[3].x) * (1.f / 6.f)),
                       p.y + (double)((k[0].y + 2.f * k[1].y + 2.f * k[2].y + k[3].y) * (1.f / 6.f)),
                       p.z + (double)((k[0].z + 2.f * k[1].z + 2.f * k[2].z + k[3].z) * (1.f / 6.f)));
-    c = ulocate(M, pn, c, r);
+    r[0] = r0[0];
+    r[1] = r0[1];
+    r[2] = r0[2];
+    c = ulocate(M, pn, c0, r, true);
     if (c < 0) {
-        float rr[3];
-        margin = ucell_param(M.cells[c0], pn, rr);
+        float rr[3] = {r0[0], r0[1], r0[2]};
+        margin = ucell_param(M.cells[c0], pn, rr, true);
         return SG_LINE_EXIT;
     }
     hint = c;
+    rp[0] = r[0];
+    rp[1] = r[1];
+    rp[2] = r[2];
     return SG_LINE_ACTIVE;
 }
 
@@ -310,7 +331,7 @@ __global__ void __launch_bounds__(256) umesh_trace_kernel(UMeshView M, UTraceArg
         int st = SG_LINE_MAXSTEPS;
         while (step < A.max_steps) {
             double3 pn;
-            const int s = urk4(M, p, A.dt, A.eps, hint, pn, margin);
+            const int s = urk4(M, p, A.dt, A.eps, hint, r, pn, margin);
             if (s != SG_LINE_ACTIVE) {
                 st = s;
                 break;
