@@ -324,6 +324,30 @@ sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t *n_vertice
                               float *vertices, uint8_t *status, float *margin, int32_t *line_source,
                               void *stream);
 
+/* Overlapped line readback into page-locked host memory (streamline and
+ * path-line tracers): the same CSR as sg_tracer_get_lines, but the copy to
+ * the host runs on the tracer's own copy stream, so that work enqueued on
+ * `stream` after this call (the next upload and trace, which may reuse every
+ * tracer buffer) overlaps it.  The call synchronises `stream` (the sizes are
+ * read), gathers the CSR into device staging memory owned by the tracer
+ * (grown on demand, freed by sg_tracer_destroy) on `stream`, and returns
+ * without waiting for the copy.  n_lines / n_vertices (host, nullable)
+ * receive the sizes; with every buffer NULL the call stops there.  Buffers
+ * (each nullable, page-locked host memory, else SG_ERR_INVALID_ARG): n_lines+1
+ * int64 offsets, 3*n_vertices floats, n_lines status bytes, n_lines float
+ * margins, as in sg_tracer_get_lines.  They are complete once a stream made
+ * to wait by sg_tracer_wait_lines has reached that point; a later overlapped
+ * readout waits (on `stream`) for the previous copy before reusing the
+ * staging memory.  SG_ERR_STATE for streakline tracers. */
+sg_status sg_tracer_get_lines_overlapped(sg_tracer *t, int64_t *n_lines, int64_t *n_vertices, int64_t *offsets,
+                                         float *vertices, uint8_t *status, float *margin, void *stream);
+
+/* Makes `stream` wait for the host copies of the last
+ * sg_tracer_get_lines_overlapped (no wait if there was none); synchronising
+ * `stream` afterwards guarantees the host buffers are complete.  Does not
+ * block the host.  SG_ERR_STATE for streakline tracers. */
+sg_status sg_tracer_wait_lines(sg_tracer *t, void *stream);
+
 /* Bidirectional readback (SG_DIR_BOTH): one polyline per seed, the backward
  * line reversed (the seed not repeated) followed by the forward line, so that
  * polyline i runs along the flow through seed i.  Two calls, as

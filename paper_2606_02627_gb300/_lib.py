@@ -95,6 +95,8 @@ SIGNATURES = {
     "sg_tracer_trace_timed": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), P, P, i32, P], i32),
     "sg_tracer_get_lines": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P, P, P], i32),
     "sg_tracer_total_steps": ([P, ctypes.POINTER(i64), P], i32),
+    "sg_tracer_get_lines_overlapped": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P, P], i32),
+    "sg_tracer_wait_lines": ([P, P], i32),
     "sg_tracer_get_joined": ([P, ctypes.POINTER(i64), ctypes.POINTER(i64), P, P, P, P], i32),
     "sg_seeds_rake": ([P, P, i64, P, P], i32),
     "sg_umesh_required_bytes": ([i64, ctypes.POINTER(ctypes.c_size_t)], i32),

@@ -290,6 +290,33 @@ class Tracer:
              _stream(stream))
         return Lines(off, vert[:nv], st[:nl], mg[:nl], src[:nl])
 
+    def get_lines_overlapped(self, out=None, stream=None) -> Lines:
+        """CSR lines into page-locked host tensors, copied on the tracer's copy
+        stream while work enqueued later on `stream` runs.  `out` (a Lines of
+        pinned tensors large enough, e.g. from an earlier call) is reused when
+        given.  The tensors are complete after wait_lines(stream) and a
+        synchronisation of `stream`."""
+        nl = ctypes.c_int64()
+        nv = ctypes.c_int64()
+        call("sg_tracer_get_lines_overlapped", self.h, ctypes.byref(nl), ctypes.byref(nv), None, None, None, None,
+             _stream(stream))
+        nl, nv = nl.value, nv.value
+        if (out is None or out.offsets.numel() < nl + 1 or out.vertices.shape[0] < nv
+                or out.status.numel() < nl or out.margin.numel() < nl):
+            off = torch.empty(nl + 1, dtype=torch.int64, pin_memory=True)
+            vert = torch.empty((max(nv, 1), 3), dtype=torch.float32, pin_memory=True)
+            st = torch.empty(max(nl, 1), dtype=torch.uint8, pin_memory=True)
+            mg = torch.empty(max(nl, 1), dtype=torch.float32, pin_memory=True)
+        else:
+            off, vert, st, mg = out.offsets, out.vertices, out.status, out.margin
+        call("sg_tracer_get_lines_overlapped", self.h, None, None, _ptr(off), _ptr(vert), _ptr(st), _ptr(mg),
+             _stream(stream))
+        return Lines(off[:nl + 1], vert[:nv], st[:nl], mg[:nl], None)
+
+    def wait_lines(self, stream=None):
+        """Makes `stream` wait for the host copies of the last overlapped readout."""
+        call("sg_tracer_wait_lines", self.h, _stream(stream))
+
     def get_joined(self, stream=None) -> JoinedLines:
         """Bidirectional tracers: one polyline per seed through the seed (device)."""
         nl = ctypes.c_int64()

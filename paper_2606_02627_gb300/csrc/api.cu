@@ -338,6 +338,9 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
             ce = cudaEventCreateWithFlags(&t->ev_gathered[k], cudaEventDisableTiming);
             if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t->ev_copied[k], cudaEventDisableTiming);
         }
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t->ev_ovl_gathered, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t->ev_ovl_copied, cudaEventDisableTiming);
+        if (ce == cudaSuccess) ce = cudaEventRecord(t->ev_ovl_copied, t->copy_stream);
         if (ce != cudaSuccess) {
             sg_tracer_destroy(t);
             return cuda_error(ce, "readback stream");
@@ -364,6 +367,12 @@ extern "C" sg_status sg_tracer_destroy(sg_tracer *t)
         if (t->ev_gathered[k]) cudaEventDestroy(t->ev_gathered[k]);
         if (t->ev_copied[k]) cudaEventDestroy(t->ev_copied[k]);
     }
+    if (t->ovl_buf) {
+        if (t->ev_ovl_copied) cudaEventSynchronize(t->ev_ovl_copied);
+        cudaFree(t->ovl_buf);
+    }
+    if (t->ev_ovl_gathered) cudaEventDestroy(t->ev_ovl_gathered);
+    if (t->ev_ovl_copied) cudaEventDestroy(t->ev_ovl_copied);
     if (t->copy_stream) cudaStreamDestroy(t->copy_stream);
     delete t;
     return SG_OK;
@@ -730,6 +739,68 @@ extern "C" sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t
         return SG_OK;
     }
     return launch_gather_lines(t, offsets, vertices, status, margin, s);
+}
+
+extern "C" sg_status sg_tracer_get_lines_overlapped(sg_tracer *t, int64_t *n_lines, int64_t *n_vertices,
+                                                    int64_t *offsets, float *vertices, uint8_t *status, float *margin,
+                                                    void *stream)
+{
+    SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
+    SG_CHECK(t->p.mode != SG_STREAKLINE, SG_ERR_STATE, "overlapped readout is for streamline and path-line tracers");
+    for (const void *q : {(const void *)offsets, (const void *)vertices, (const void *)status, (const void *)margin})
+        SG_CHECK(!q || pointer_kind(q) == PTR_PINNED, SG_ERR_INVALID_ARG,
+                 "overlapped readout buffers must be page-locked host memory");
+    SG_CUDA(cudaSetDevice(t->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    sg_status st = ensure_scanned(t, s);
+    if (st) return st;
+    int64_t tot[3];
+    if ((st = read_totals(t, tot, s))) return st;   // synchronises `stream`: the trace is done
+    if (n_lines) *n_lines = tot[1];
+    if (n_vertices) *n_vertices = tot[0];
+    if (!offsets && !vertices && !status && !margin) return SG_OK;
+    const size_t nl = (size_t)t->n_lines, nv = (size_t)tot[0];
+    const size_t o_off = 0, o_vert = align_up(sizeof(int64_t) * (nl + 1), 256);
+    const size_t o_st = o_vert + align_up(sizeof(float) * 3 * nv, 256);
+    const size_t o_mg = o_st + align_up(nl, 256);
+    const size_t need = o_mg + align_up(sizeof(float) * nl, 256);
+    if (need > t->ovl_bytes) {
+        // the previous copy still reads the old buffer
+        SG_CUDA(cudaEventSynchronize(t->ev_ovl_copied));
+        if (t->ovl_buf) SG_CUDA(cudaFree(t->ovl_buf));
+        t->ovl_buf = nullptr;
+        t->ovl_bytes = 0;
+        const size_t bytes = align_up(need, (size_t)2 << 20);
+        SG_CUDA(cudaMalloc(&t->ovl_buf, bytes));
+        t->ovl_bytes = bytes;
+    }
+    char *b = t->ovl_buf;
+    // the gather overwrites the staging memory only after the previous copy read it
+    SG_CUDA(cudaStreamWaitEvent(s, t->ev_ovl_copied, 0));
+    st = launch_gather_lines(t, (int64_t *)(b + o_off), (float *)(b + o_vert), (uint8_t *)(b + o_st),
+                             (float *)(b + o_mg), s);
+    if (st) return st;
+    SG_CUDA(cudaEventRecord(t->ev_ovl_gathered, s));
+    SG_CUDA(cudaStreamWaitEvent(t->copy_stream, t->ev_ovl_gathered, 0));
+    if (offsets)
+        SG_CUDA(cudaMemcpyAsync(offsets, b + o_off, sizeof(int64_t) * (nl + 1), cudaMemcpyDeviceToHost,
+                                t->copy_stream));
+    if (vertices && nv)
+        SG_CUDA(cudaMemcpyAsync(vertices, b + o_vert, sizeof(float) * 3 * nv, cudaMemcpyDeviceToHost, t->copy_stream));
+    if (status && nl) SG_CUDA(cudaMemcpyAsync(status, b + o_st, nl, cudaMemcpyDeviceToHost, t->copy_stream));
+    if (margin && nl)
+        SG_CUDA(cudaMemcpyAsync(margin, b + o_mg, sizeof(float) * nl, cudaMemcpyDeviceToHost, t->copy_stream));
+    SG_CUDA(cudaEventRecord(t->ev_ovl_copied, t->copy_stream));
+    return SG_OK;
+}
+
+extern "C" sg_status sg_tracer_wait_lines(sg_tracer *t, void *stream)
+{
+    SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
+    SG_CHECK(t->p.mode != SG_STREAKLINE, SG_ERR_STATE, "overlapped readout is for streamline and path-line tracers");
+    SG_CUDA(cudaSetDevice(t->ctx->device));
+    SG_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, t->ev_ovl_copied, 0));
+    return SG_OK;
 }
 
 extern "C" sg_status sg_tracer_get_joined(sg_tracer *t, int64_t *n_lines, int64_t *n_vertices, int64_t *offsets,

@@ -133,6 +133,12 @@ struct sg_tracer {
     cudaStream_t copy_stream;
     cudaEvent_t ev_gathered[2];
     cudaEvent_t ev_copied[2];
+    // overlapped readout: the whole CSR gathered into device memory, then
+    // copied to the host on copy_stream while the caller's stream moves on
+    char *ovl_buf;               // device, grown on demand
+    size_t ovl_bytes;
+    cudaEvent_t ev_ovl_gathered;
+    cudaEvent_t ev_ovl_copied;
     // streaklines
     int64_t n_release;
     int32_t births;              // births released so far

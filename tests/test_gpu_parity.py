@@ -348,6 +348,49 @@ def test_lines_to_pinned_host_and_total_steps(ctx, turb64):
     compare_lines(dev, g, ref, tol=FP32_TOL)
 
 
+def test_overlapped_readout_pipelined(ctx, turb64):
+    """The host copy of trace k overlaps trace k+1 on the same tracer: both
+    host results equal the synchronous device readouts."""
+    g, F, seeds, dt, ref = turb64
+    from paper_2606_02627_gb300 import api, _lib
+    fld = make_field(ctx, g, F, bricks=(4, 4, 4), layout="cell8")
+    tr = api.Tracer(ctx, fld, capacity=len(seeds), dt=dt, max_steps=1000)
+    s = torch.cuda.current_stream()
+    other = inputs.uniform_seeds(g, len(seeds) // 2, 7)
+    dev_ref = []
+    for sd in (seeds, other):
+        tr.upload_seeds(sd)
+        tr.trace()
+        L = tr.get_lines()
+        torch.cuda.synchronize()
+        dev_ref.append((L.offsets.cpu(), L.vertices.cpu(), L.status.cpu(), L.margin.cpu()))
+    outs = []
+    pinned = [torch.from_numpy(sd).pin_memory() for sd in (seeds, other)]
+    for k in range(3):
+        tr.upload_seeds(pinned[k % 2], stream=s)
+        tr.trace(stream=s)
+        outs.append(tr.get_lines_overlapped(stream=s))   # the next trace is enqueued before its copy is waited for
+    tr.wait_lines(s)
+    s.synchronize()
+    for k, out in enumerate(outs):
+        o, v, st, mg = dev_ref[k % 2]
+        assert torch.equal(out.offsets, o)
+        assert torch.equal(out.vertices, v)
+        assert torch.equal(out.status, st)
+        assert torch.equal(out.margin, mg)
+    compare_lines(outs[2], g, ref, tol=FP32_TOL)
+    # reuse of the host buffers, and the empty trace
+    tr.upload_seeds(torch.zeros((0, 3)).cuda())
+    tr.trace()
+    e = tr.get_lines_overlapped(out=outs[0])
+    tr.wait_lines()
+    torch.cuda.synchronize()
+    assert e.offsets.tolist() == [0] and e.vertices.shape[0] == 0
+    with pytest.raises(_lib.StreamGBError):             # pageable host memory is refused
+        api.call("sg_tracer_get_lines_overlapped", tr.h, None, None, np.zeros(4, np.int64).ctypes.data,
+                 None, None, None, None)
+
+
 def test_invalid_arguments(ctx):
     from paper_2606_02627_gb300 import api, _lib
     g = inputs.cube_grid(8)
