@@ -176,8 +176,9 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
     unsigned parity = 0, waited = 0;
     int c[3] = {0, 0, 0}, q[3] = {0, 0, 0};               // P0 and the current sample point
     float f[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};
-    float k1[3] = {0.f, 0.f, 0.f}, k2[3] = {0.f, 0.f, 0.f}, k3[3] = {0.f, 0.f, 0.f};
-    float ds[3] = {0.f, 0.f, 0.f};
+    // k1-k3 and ds: x and y as packed pairs, z alone
+    f32x2 k1xy = 0, k2xy = 0, k3xy = 0, dsxy = 0;
+    float k1z = 0.f, k2z = 0.f, k3z = 0.f, dsz = 0.f;
     uint32_t line = 0, step = 0, here = 0, stage = 0;
     uint32_t held = 0xffffffffu, wanted = 0;              // cell of the record in the slot / in flight
     BrickRef<DT> br;
@@ -216,12 +217,15 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
                     brick_of<DT>(F, c, br);
                     float dtc[3];
                     line_dtc(P, line, dtc);
+                    float ds[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         ds[a] = (DT == SG_F32) ? dtc[a] : __fmul_rn(dtc[a], br.scale);
                         q[a] = c[a];
                         g[a] = f[a];
                     }
+                    dsxy = pk2(ds[0], ds[1]);
+                    dsz = ds[2];
                     active = true;
                     here = 0;
                     stage = 0;
@@ -278,20 +282,27 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
             for (int k = 0; k < NCH; ++k) R.r[k] = slots[k * nthr + tid];
             bool bad;
             const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad);
-            float sp = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
+            const f32x2 vxy = pk2(v.x, v.y);
+            const float2 sq = upk2(mul2(vxy, vxy));
+            float sp = sqrtf(__fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z)));
             if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
-            const float k[3] = {__fmul_rn(v.x, ds[0]), __fmul_rn(v.y, ds[1]), __fmul_rn(v.z, ds[2])};
+            const f32x2 kxy = mul2(vxy, dsxy);
+            const float kz = __fmul_rn(v.z, dsz);
             const bool last = stage == 3;
             const float w = stage < 2 ? 0.5f : 1.0f;   // P1, P2 = P0 + k/2; P3 = P0 + k3
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float fin =
-                    __fmul_rn(__fadd_rn(__fadd_rn(k1[a], k[a]), __fmul_rn(2.0f, __fadd_rn(k2[a], k3[a]))), 1.0f / 6.0f);
-                locate(f[a], last ? fin : w * k[a], c[a], q[a], g[a]);
-                k1[a] = stage == 0 ? k[a] : k1[a];
-                k2[a] = stage == 1 ? k[a] : k2[a];
-                k3[a] = stage == 2 ? k[a] : k3[a];
-            }
+            const float2 fin = upk2(mul2(add2(add2(k1xy, kxy), mul2(pk2(2.0f, 2.0f), add2(k2xy, k3xy))),
+                                         pk2(1.0f / 6.0f, 1.0f / 6.0f)));
+            const float finz = __fmul_rn(__fadd_rn(__fadd_rn(k1z, kz), __fmul_rn(2.0f, __fadd_rn(k2z, k3z))), 1.0f / 6.0f);
+            const float2 wk = upk2(mul2(pk2(w, w), kxy));
+            locate(f[0], last ? fin.x : wk.x, c[0], q[0], g[0]);
+            locate(f[1], last ? fin.y : wk.y, c[1], q[1], g[1]);
+            locate(f[2], last ? finz : w * kz, c[2], q[2], g[2]);
+            k1xy = stage == 0 ? kxy : k1xy;
+            k2xy = stage == 1 ? kxy : k2xy;
+            k3xy = stage == 2 ? kxy : k3xy;
+            k1z = stage == 0 ? kz : k1z;
+            k2z = stage == 1 ? kz : k2z;
+            k3z = stage == 2 ? kz : k3z;
             if (bad) {
                 st = SG_LINE_NANFIELD;
             } else if (stage == 0 && sp < P.eps) {

@@ -220,6 +220,51 @@ __device__ __forceinline__ typename Elem<DT>::T load_elem(const typename Elem<DT
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
+// Two FP32 values in one 64-bit register pair, with the packed FP32
+// arithmetic of sm_100 and later: one instruction does the operation on both
+// halves, each rounded as the scalar instruction (round to nearest, no flush
+// of subnormals), so packed and scalar code give the same bits.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(f32x2 v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// lerpf on both halves
+__device__ __forceinline__ f32x2 lerp2(f32x2 a, f32x2 b, f32x2 t) { return fma2(t, sub2(b, a), a); }
+
 // Storage offset of a sample inside a brick (fits in 32 bits: checked when the
 // field is created), separable per axis: off = ox(x) + oy(y) + oz(z).
 template <int LAYOUT>
@@ -258,11 +303,16 @@ __device__ __forceinline__ float3 lerp8(const float3 &c000, const float3 &c100, 
                                         const float3 &c001, const float3 &c101, const float3 &c011, const float3 &c111,
                                         float fx, float fy, float fz)
 {
+    // x and y components as packed pairs, z alone: the same operations per
+    // component as three scalar lerp trees
+    const f32x2 tx = pk2(fx, fx), ty = pk2(fy, fy), tz = pk2(fz, fz);
+    auto xy = [](const float3 &c) { return pk2(c.x, c.y); };
+    const f32x2 rxy = lerp2(lerp2(lerp2(xy(c000), xy(c100), tx), lerp2(xy(c010), xy(c110), tx), ty),
+                            lerp2(lerp2(xy(c001), xy(c101), tx), lerp2(xy(c011), xy(c111), tx), ty), tz);
+    const float2 v = upk2(rxy);
     float3 r;
-    r.x = lerpf(lerpf(lerpf(c000.x, c100.x, fx), lerpf(c010.x, c110.x, fx), fy),
-                lerpf(lerpf(c001.x, c101.x, fx), lerpf(c011.x, c111.x, fx), fy), fz);
-    r.y = lerpf(lerpf(lerpf(c000.y, c100.y, fx), lerpf(c010.y, c110.y, fx), fy),
-                lerpf(lerpf(c001.y, c101.y, fx), lerpf(c011.y, c111.y, fx), fy), fz);
+    r.x = v.x;
+    r.y = v.y;
     r.z = lerpf(lerpf(lerpf(c000.z, c100.z, fx), lerpf(c010.z, c110.z, fx), fy),
                 lerpf(lerpf(c001.z, c101.z, fx), lerpf(c011.z, c111.z, fx), fy), fz);
     return r;
@@ -352,16 +402,24 @@ __device__ __forceinline__ float3 interp_record(const Record<DT> &R, float fx, f
                                __int_as_float(0x4B000000u | (__funnelshift_r(lo, hi, 21) & FX21_MASK)),
                                __int_as_float(0x4B000000u | (hi >> 11)));
         };
-        auto xl = [&](float3 p, float3 q) {
-            return make_float3(fmaf(fx, q.x - p.x, p.x - C), fmaf(fx, q.y - p.y, p.y - C), fmaf(fx, q.z - p.z, p.z - C));
+        // x and y components as packed pairs, z alone
+        const f32x2 tx = pk2(fx, fx), ty = pk2(fy, fy), tz = pk2(fz, fz), C2 = pk2(C, C);
+        struct X {
+            f32x2 xy;
+            float z;
         };
-        const float3 x00 = xl(raw(a.x, a.y), raw(a.z, a.w));   // (y0, z0)
-        const float3 x10 = xl(raw(b.x, b.y), raw(b.z, b.w));   // (y1, z0)
-        const float3 x01 = xl(raw(c.x, c.y), raw(c.z, c.w));   // (y0, z1)
-        const float3 x11 = xl(raw(d.x, d.y), raw(d.z, d.w));   // (y1, z1)
+        auto xl = [&](float3 p, float3 q) {
+            const f32x2 pxy = pk2(p.x, p.y);
+            return X{fma2(tx, sub2(pk2(q.x, q.y), pxy), sub2(pxy, C2)), fmaf(fx, q.z - p.z, p.z - C)};
+        };
+        const X x00 = xl(raw(a.x, a.y), raw(a.z, a.w));   // (y0, z0)
+        const X x10 = xl(raw(b.x, b.y), raw(b.z, b.w));   // (y1, z0)
+        const X x01 = xl(raw(c.x, c.y), raw(c.z, c.w));   // (y0, z1)
+        const X x11 = xl(raw(d.x, d.y), raw(d.z, d.w));   // (y1, z1)
+        const float2 vxy = upk2(lerp2(lerp2(x00.xy, x10.xy, ty), lerp2(x01.xy, x11.xy, ty), tz));
         float3 v;
-        v.x = lerpf(lerpf(x00.x, x10.x, fy), lerpf(x01.x, x11.x, fy), fz);
-        v.y = lerpf(lerpf(x00.y, x10.y, fy), lerpf(x01.y, x11.y, fy), fz);
+        v.x = vxy.x;
+        v.y = vxy.y;
         v.z = lerpf(lerpf(x00.z, x10.z, fy), lerpf(x01.z, x11.z, fy), fz);
         bad = ((a.y | a.w | b.y | b.w | c.y | c.w | d.y | d.w) & FX21_FLAG) != 0u;
         return v;
