@@ -427,7 +427,7 @@ def main():
                           f"max {args.max_steps} steps",
               "field": f"{n}^3", "bricks": "4x4x4", "seeds_per_gpu": args.seeds, "max_steps": args.max_steps,
               "h_cells": args.h, "field_storage": args.dtype, "layout": args.layout,
-              "l2": "inputs larger than L2 (field 1.6 GB; cell records 18 GB FP32, 9 GB 8-byte formats; "
+              "l2": "inputs larger than L2 (field 1.6 GB; cell records 13.5 GB FP32, 9 GB 8-byte formats; "
                     "slabs 24 GB)",
               "parallelism": f"replicas x{world} (seeds per rank, field replicated)"}
 

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
         const int sx = q[0] - br.lo[0] + 1, sy = q[1] - br.lo[1] + 1, sz = q[2] - br.lo[2] + 1;
         const uint32_t cell = (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
         if (cell != held) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(br.data + (long long)cell * 8);
+            const uint4 *src = reinterpret_cast<const uint4 *>(br.data + (long long)cell * record_elems<DT>());
 #pragma unroll
             for (int k = 0; k < NCH; ++k) cp_async16(slot + k * nthr * 16u, src + k);
             cp_async_arrive(bar);

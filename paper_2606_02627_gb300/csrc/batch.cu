@@ -173,11 +173,11 @@ __global__ void __launch_bounds__(256) batch_round_kernel(const __grid_constant_
 
 // The same round with the lanes of a warp decoupled (CELL8 layout), as the
 // tracer's round_async_kernel: each lane keeps the cell record of its current
-// sample point in its own shared-memory slot (8 chunks of 16 B, enough for
+// sample point in its own shared-memory slot (6 chunks of 16 B, enough for
 // FP32; the 8-byte formats use 4), fetches another with cp.async completing
 // on its own mbarrier, and runs one RK4 stage per pass; the storage type of
 // each lane's request selects the decode.  Stage arithmetic as rk4_bricked's.
-constexpr int BATCH_SLOT_CHUNKS = 8;
+constexpr int BATCH_SLOT_CHUNKS = Record<SG_F32>::chunks;
 // Consecutive passes a lane may wait for one record copy (each pass takes at
 // least ~100 cycles: well over a second in all), as in the tracer's kernel.
 constexpr unsigned BATCH_COPY_WAIT_PASSES = 1u << 24;
@@ -207,7 +207,7 @@ __device__ __forceinline__ float3 interp_slot(int dtype, const uint4 *slots, uns
     default: {
         Record<SG_F32> R;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) R.r[k] = slots[k * nthr + tid];
+        for (int k = 0; k < Record<SG_F32>::chunks; ++k) R.r[k] = slots[k * nthr + tid];
         return interp_record<SG_F32>(R, fx, fy, fz, bad);
     }
     }
@@ -215,7 +215,7 @@ __device__ __forceinline__ float3 interp_slot(int dtype, const uint4 *slots, uns
 
 __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant__ BatchParams P)
 {
-    extern __shared__ uint4 slots[];                       // [8][blockDim] chunks, then blockDim barriers
+    extern __shared__ uint4 slots[];                       // [6][blockDim] chunks, then blockDim barriers
     const unsigned tid = threadIdx.x, nthr = blockDim.x;
     const unsigned lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
         const int sx = q[0] - br.lo[0] + 1, sy = q[1] - br.lo[1] + 1, sz = q[2] - br.lo[2] + 1;
         const uint32_t cell = (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
         if (cell != held) {
-            const int nch = dtype == SG_F32 ? 8 : 4;
+            const int nch = dtype == SG_F32 ? Record<SG_F32>::chunks : Record<SG_F16>::chunks;
             const uint4 *src = reinterpret_cast<const uint4 *>(br.data) + (long long)cell * nch;
             for (int k = 0; k < nch; ++k) cp_async16(slot + k * nthr * 16u, src + k);
             cp_async_arrive(bar);

@@ -291,7 +291,8 @@ inline __host__ __device__ long long storage_index(int layout, int x, int y, int
     if (layout == SG_LAYOUT_LINEAR) return ((long long)z * F.S[1] + y) * F.S[0] + x;
     if (layout == SG_LAYOUT_CELL8) {
         // the copy of sample (x,y,z) held by the cell whose lower corner it is
-        // (the last cell for the upper layer)
+        // (the last cell for the upper layer); 8-byte samples only (FP32
+        // records split the components: cell8_f32_index)
         const int cx = x < F.C[0] ? x : F.C[0] - 1, cy = y < F.C[1] ? y : F.C[1] - 1, cz = z < F.C[2] ? z : F.C[2] - 1;
         const int corner = (x - cx) | ((y - cy) << 1) | ((z - cz) << 2);
         return (((long long)cz * F.C[1] + cy) * F.C[0] + cx) * 8 + corner;
@@ -367,13 +368,37 @@ __device__ __forceinline__ bool mbar_done(uint32_t bar, unsigned parity)
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// A cell record (CELL8 layout) as 16-byte chunks: 4 for 8-byte samples, 8 for
-// FP32 (float4 samples).
+// A cell record (CELL8 layout) as 16-byte chunks.  8-byte samples: 4 chunks,
+// chunk j holding corners 2j and 2j+1 (corner k = (x, y, z) = (k & 1,
+// k >> 1 & 1, k >> 2) from the cell's lower corner).  FP32: 6 chunks, one
+// component after the other (x, y, z), each as two chunks: the four corners
+// with x = 0, then the four with x = 1, each chunk in the order (y, z) =
+// (0,0), (0,1), (1,0), (1,1).  That order puts the two z corners of one
+// (x, y) edge side by side, so the x and y lerps run on packed pairs.
 template <int DT>
 struct Record {
-    static constexpr int chunks = (DT == SG_F32) ? 8 : 4;
+    static constexpr int chunks = (DT == SG_F32) ? 6 : 4;
     uint4 r[chunks];
 };
+
+// Elements (Elem<DT>::T) from one record to the next.
+template <int DT>
+__host__ __device__ constexpr int record_elems() { return DT == SG_F32 ? 6 : 8; }
+
+// Float index of component a of corner (dx, dy, dz) within an FP32 record.
+inline __host__ __device__ int f32_record_index(int a, int dx, int dy, int dz)
+{
+    return a * 8 + dx * 4 + dy * 2 + dz;
+}
+
+// Float index of component a of sample (x, y, z) in an FP32 CELL8 brick: the
+// copy held by the cell whose lower corner it is (the last cell for the upper
+// layer), as storage_index.
+inline __host__ __device__ long long cell8_f32_index(int x, int y, int z, int a, const DevField &F)
+{
+    const int cx = x < F.C[0] ? x : F.C[0] - 1, cy = y < F.C[1] ? y : F.C[1] - 1, cz = z < F.C[2] ? z : F.C[2] - 1;
+    return (((long long)cz * F.C[1] + cy) * F.C[0] + cx) * 24 + f32_record_index(a, x - cx, y - cy, z - cz);
+}
 
 // Reads one record: 32-byte loads (records are 64-byte aligned).
 template <int DT>
@@ -424,11 +449,19 @@ __device__ __forceinline__ float3 interp_record(const Record<DT> &R, float fx, f
         bad = ((a.y | a.w | b.y | b.w | c.y | c.w | d.y | d.w) & FX21_FLAG) != 0u;
         return v;
     } else if constexpr (DT == SG_F32) {
-        auto f4 = [](uint4 x) { return make_float4(__uint_as_float(x.x), __uint_as_float(x.y), __uint_as_float(x.z),
-                                                   __uint_as_float(x.w)); };
-        const float3 v = lerp8(decode_elem<DT>(f4(R.r[0])), decode_elem<DT>(f4(R.r[1])), decode_elem<DT>(f4(R.r[2])),
-                               decode_elem<DT>(f4(R.r[3])), decode_elem<DT>(f4(R.r[4])), decode_elem<DT>(f4(R.r[5])),
-                               decode_elem<DT>(f4(R.r[6])), decode_elem<DT>(f4(R.r[7])), fx, fy, fz);
+        // per component: x lerps of the (z0, z1) pairs at y0 and at y1, one y
+        // lerp of the two results, the z lerp of its halves; the same
+        // operations as lerp8
+        const f32x2 tx = pk2(fx, fx), ty = pk2(fy, fy);
+        auto comp = [&](uint4 lo, uint4 hi) {
+            const f32x2 y0 = lerp2(pk2(__uint_as_float(lo.x), __uint_as_float(lo.y)),
+                                   pk2(__uint_as_float(hi.x), __uint_as_float(hi.y)), tx);
+            const f32x2 y1 = lerp2(pk2(__uint_as_float(lo.z), __uint_as_float(lo.w)),
+                                   pk2(__uint_as_float(hi.z), __uint_as_float(hi.w)), tx);
+            const float2 z = upk2(lerp2(y0, y1, ty));
+            return lerpf(z.x, z.y, fz);
+        };
+        const float3 v = make_float3(comp(R.r[0], R.r[1]), comp(R.r[2], R.r[3]), comp(R.r[4], R.r[5]));
         bad = bad3(v);
         return v;
     } else {
@@ -462,7 +495,7 @@ __device__ __forceinline__ float3 trilerp(const typename Elem<DT>::T *__restrict
 {
     if constexpr (LAYOUT == SG_LAYOUT_CELL8) {
         const int cell = (sz * F.C[1] + sy) * F.C[0] + sx;
-        return trilerp_record<DT>(brick + (long long)cell * 8, fx, fy, fz, bad);
+        return trilerp_record<DT>(brick + (long long)cell * record_elems<DT>(), fx, fy, fz, bad);
     } else {
         using O = Offsets<LAYOUT>;
         const int x0 = O::ox(sx, F), x1 = O::ox(sx + 1, F);

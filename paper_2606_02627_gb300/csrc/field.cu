@@ -191,8 +191,8 @@ template <int DT>
 __global__ void brick_store_cell8_kernel(StoreArgs A)
 {
     using T = typename Elem<DT>::T;
-    constexpr int CPR = (DT == SG_F32) ? 8 : 4;    // chunks per record
-    constexpr int KPC = 8 / CPR;                    // corners per chunk
+    constexpr int CPR = Record<DT>::chunks;         // chunks per record
+    constexpr int KPC = 2;                          // corners per chunk (8-byte samples)
     const DevField &F = A.F;
     const int b = A.brick0 + blockIdx.y;
     const int bx = b % F.B[0], by = (b / F.B[0]) % F.B[1], bz = b / (F.B[0] * F.B[1]);
@@ -206,26 +206,31 @@ __global__ void brick_store_cell8_kernel(StoreArgs A)
         uint4 *dst = brick + (long long)r * row_chunks;
         for (int j = threadIdx.x; j < row_chunks; j += blockDim.x) {
             const int cx = j / CPR, jc = j % CPR;
-            T e[KPC];
-#pragma unroll
-            for (int m = 0; m < KPC; ++m) {
-                const int k = jc * KPC + m;
-                const float *src;
-                if (A.src_mode == 1) {
-                    src = A.src + 3 * (((long long)(cz + (k >> 2)) * F.S[1] + cy + ((k >> 1) & 1)) * F.S[0] + cx +
-                                       (k & 1));
-                } else {
-                    const int gx = clampi(x0 + cx + (k & 1), 0, F.nm1[0]);
-                    const int gy = clampi(by * F.n[1] - 1 + cy + ((k >> 1) & 1), 0, F.nm1[1]);
-                    const int gz = clampi(bz * F.n[2] - 1 + cz + (k >> 2), 0, F.nm1[2]);
-                    src = A.src + 3 * (((long long)gz * F.dims[1] + gy) * F.dims[0] + gx);
-                }
-                e[m] = encode_elem<DT>(src[0], src[1], src[2], s);
-            }
+            // the source sample of corner (dx, dy, dz)
+            auto corner = [&](int dx, int dy, int dz) -> const float * {
+                if (A.src_mode == 1)
+                    return A.src + 3 * (((long long)(cz + dz) * F.S[1] + cy + dy) * F.S[0] + cx + dx);
+                const int gx = clampi(x0 + cx + dx, 0, F.nm1[0]);
+                const int gy = clampi(by * F.n[1] - 1 + cy + dy, 0, F.nm1[1]);
+                const int gz = clampi(bz * F.n[2] - 1 + cz + dz, 0, F.nm1[2]);
+                return A.src + 3 * (((long long)gz * F.dims[1] + gy) * F.dims[0] + gx);
+            };
             uint4 out;
-            if constexpr (DT == SG_F32) out = make_uint4(__float_as_uint(e[0].x), __float_as_uint(e[0].y),
-                                                         __float_as_uint(e[0].z), __float_as_uint(e[0].w));
-            else out = make_uint4(e[0].x, e[0].y, e[1].x, e[1].y);
+            if constexpr (DT == SG_F32) {
+                // component a = jc / 2 of the four corners with x = jc % 2
+                const int a = jc >> 1, dx = jc & 1;
+                out = make_uint4(__float_as_uint(corner(dx, 0, 0)[a]), __float_as_uint(corner(dx, 0, 1)[a]),
+                                 __float_as_uint(corner(dx, 1, 0)[a]), __float_as_uint(corner(dx, 1, 1)[a]));
+            } else {
+                T e[KPC];
+#pragma unroll
+                for (int m = 0; m < KPC; ++m) {
+                    const int k = jc * KPC + m;
+                    const float *src = corner(k & 1, (k >> 1) & 1, k >> 2);
+                    e[m] = encode_elem<DT>(src[0], src[1], src[2], s);
+                }
+                out = make_uint4(e[0].x, e[0].y, e[1].x, e[1].y);
+            }
             dst[j] = out;
         }
     }
@@ -253,7 +258,14 @@ __global__ void max_speed_kernel(DevField F, long long brick_bytes, int layout, 
         const int sx = (int)(r % F.S[0]);
         const int sy = (int)((r / F.S[0]) % F.S[1]);
         const int sz = (int)(r / ((long long)F.S[0] * F.S[1]));
-        const float3 v = decode_elem<DT>(brick[storage_index(layout, sx, sy, sz, F)]);
+        float3 v;
+        if (DT == SG_F32 && layout == SG_LAYOUT_CELL8) {
+            const float *bf = reinterpret_cast<const float *>(brick);
+            v = make_float3(bf[cell8_f32_index(sx, sy, sz, 0, F)], bf[cell8_f32_index(sx, sy, sz, 1, F)],
+                            bf[cell8_f32_index(sx, sy, sz, 2, F)]);
+        } else {
+            v = decode_elem<DT>(brick[storage_index(layout, sx, sy, sz, F)]);
+        }
         const float x = v.x * s * isx, y = v.y * s * isy, z = v.z * s * isz;
         const float sp = sqrtf(x * x + y * y + z * z);
         if (sp < INFINITY && sp > m) m = sp;
@@ -413,7 +425,8 @@ static sg_status field_layout(const sg_field_desc *d, sg_field *f, size_t *bytes
         elem = d->dtype == SG_F32 ? 16 : 8;
         if (d->layout == SG_LAYOUT_LINEAR) g.brick_elems = (long long)g.S[0] * g.S[1] * g.S[2];
         else if (d->layout == SG_LAYOUT_TILED4) g.brick_elems = (long long)g.T[0] * g.T[1] * g.T[2] * 64;
-        else g.brick_elems = (long long)g.C[0] * g.C[1] * g.C[2] * 8;
+        else g.brick_elems = (long long)g.C[0] * g.C[1] * g.C[2] * (d->dtype == SG_F32 ? record_elems<SG_F32>()
+                                                                                      : record_elems<SG_F16>());
         SG_CHECK(g.brick_elems < (1ll << 31) - 1, SG_ERR_UNSUPPORTED, "a brick holds more than 2^31 samples");
         SG_CHECK(nb <= 65535, SG_ERR_UNSUPPORTED, "more than 65535 bricks");
         brick_bytes = align_up((size_t)g.brick_elems * elem, 256);
@@ -627,7 +640,11 @@ extern "C" sg_status sg_field_read_brick(sg_field *f, int32_t slot, int32_t bx, 
             for (int x = 0; x < g.S[0]; ++x) {
                 const long long src = storage_index(f->desc.layout, x, y, z, g);
                 const long long dst = 3 * (((long long)z * g.S[1] + y) * g.S[0] + x);
-                if (f->desc.dtype == SG_F32) {
+                if (f->desc.dtype == SG_F32 && f->desc.layout == SG_LAYOUT_CELL8) {
+                    const float *v = reinterpret_cast<const float *>(raw);
+                    float *o = reinterpret_cast<float *>(out) + dst;
+                    for (int a = 0; a < 3; ++a) o[a] = v[cell8_f32_index(x, y, z, a, g)];
+                } else if (f->desc.dtype == SG_F32) {
                     const float *v = reinterpret_cast<const float *>(raw) + 4 * src;
                     float *o = reinterpret_cast<float *>(out) + dst;
                     o[0] = v[0];
