@@ -153,7 +153,7 @@ constexpr unsigned COPY_WAIT_PASSES = 1u << 24;
 // rk4_bricked's, operation for operation, so both kernels produce the same
 // bits.
 template <int DT>
-__global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant__ LineParams P)
+__global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel(const __grid_constant__ LineParams P)
 {
     constexpr int NCH = Record<DT>::chunks;
     extern __shared__ uint4 slots[];                       // [NCH][blockDim] chunks, then blockDim barriers
@@ -185,21 +185,30 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
     br.data = nullptr;
     br.scale = 1.0f;
     for (int a = 0; a < 3; ++a) br.lo[a] = br.hi[a] = 0;
+    // cells [box_lo, box_lo + box_span] per axis lie inside the domain's
+    // cells (not on its last sample layer) and inside the brick's ghost
+    // shell: a stage point there needs neither the EXIT nor the HALO test
+    int box_lo[3] = {0, 0, 0};
+    unsigned box_span[3] = {0u, 0u, 0u};
+    // |v|^2 at or above e2min (before the brick scale) means |v| >= eps
+    float e2min = 0.f;
+    float *vp = nullptr;                                   // where the line's next vertex goes
 
-    // the record of sample point q into the slot, unless it is there already
-    auto fetch = [&]() {
+    // the cell of sample point q within the brick's records
+    auto cell_of = [&]() {
         const int sx = q[0] - br.lo[0] + 1, sy = q[1] - br.lo[1] + 1, sz = q[2] - br.lo[2] + 1;
-        const uint32_t cell = (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
-        if (cell != held) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(br.data + (long long)cell * record_elems<DT>());
+        return (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
+    };
+    // copy the record of `cell` into the slot
+    auto fetch = [&](uint32_t cell) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(br.data + (long long)cell * record_elems<DT>());
 #pragma unroll
-            for (int k = 0; k < NCH; ++k) cp_async16(slot + k * nthr * 16u, src + k);
-            cp_async_arrive(bar);
-            held = 0xffffffffu;
-            wanted = cell;
-            pending = true;
-            waited = 0;
-        }
+        for (int k = 0; k < NCH; ++k) cp_async16(slot + k * nthr * 16u, src + k);
+        cp_async_arrive(bar);
+        held = 0xffffffffu;
+        wanted = cell;
+        pending = true;
+        waited = 0;
     };
 
     while (true) {
@@ -226,11 +235,23 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
                     }
                     dsxy = pk2(ds[0], ds[1]);
                     dsz = ds[2];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int lo = max(br.lo[a] - 1, 0);
+                        const int hi = min(br.lo[a] + F.S[a] - 3, F.nm1[a] - 1);
+                        box_lo[a] = lo;
+                        box_span[a] = hi >= lo ? (unsigned)(hi - lo) : 0u;
+                        if (hi < lo) box_lo[a] = 0x7fffffff;   // empty: every point takes the full tests
+                    }
+                    {
+                        const float e = (DT == SG_F32) ? P.eps : __fdiv_ru(P.eps, br.scale);
+                        e2min = __fmul_ru(e, e);
+                    }
+                    vp = P.slab + ((long long)line * P.W + step + 1) * 3;
                     active = true;
                     here = 0;
                     stage = 0;
-                    held = 0xffffffffu;            // another brick: the slot's record is stale
-                    fetch();
+                    fetch(cell_of());                // another brick: the slot's record is stale
                 }
             }
         }
@@ -284,8 +305,7 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
             const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad);
             const f32x2 vxy = pk2(v.x, v.y);
             const float2 sq = upk2(mul2(vxy, vxy));
-            float sp = sqrtf(__fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z)));
-            if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
+            const float s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
             const f32x2 kxy = mul2(vxy, dsxy);
             const float kz = __fmul_rn(v.z, dsz);
             const bool last = stage == 3;
@@ -303,18 +323,27 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
             k1z = stage == 0 ? kz : k1z;
             k2z = stage == 1 ? kz : k2z;
             k3z = stage == 2 ? kz : k3z;
-            if (bad) {
-                st = SG_LINE_NANFIELD;
-            } else if (stage == 0 && sp < P.eps) {
-                margin = (P.eps - sp) / P.eps;
-                st = SG_LINE_STAGNANT;
-            } else if (!in_domain(F, q, g)) {
-                margin = out_dist(F, q, g);
-                st = SG_LINE_EXIT;
-            } else if (!last && ((unsigned)(q[0] - br.lo[0] + 1) > (unsigned)(F.S[0] - 2) ||
-                                 (unsigned)(q[1] - br.lo[1] + 1) > (unsigned)(F.S[1] - 2) ||
-                                 (unsigned)(q[2] - br.lo[2] + 1) > (unsigned)(F.S[2] - 2))) {
-                st = SG_LINE_HALO;
+            const bool in_box = (unsigned)(q[0] - box_lo[0]) <= box_span[0] &&
+                                (unsigned)(q[1] - box_lo[1]) <= box_span[1] &&
+                                (unsigned)(q[2] - box_lo[2]) <= box_span[2];
+            if (bad || (stage == 0 && !(s2 >= e2min)) || !in_box) {
+                // the tests in full (rare): a non-finite sample, a speed that
+                // may be below eps, a point near the domain or brick boundary
+                float sp = sqrtf(s2);
+                if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
+                if (bad) {
+                    st = SG_LINE_NANFIELD;
+                } else if (stage == 0 && sp < P.eps) {
+                    margin = (P.eps - sp) / P.eps;
+                    st = SG_LINE_STAGNANT;
+                } else if (!in_domain(F, q, g)) {
+                    margin = out_dist(F, q, g);
+                    st = SG_LINE_EXIT;
+                } else if (!last && ((unsigned)(q[0] - br.lo[0] + 1) > (unsigned)(F.S[0] - 2) ||
+                                     (unsigned)(q[1] - br.lo[1] + 1) > (unsigned)(F.S[1] - 2) ||
+                                     (unsigned)(q[2] - br.lo[2] + 1) > (unsigned)(F.S[2] - 2))) {
+                    st = SG_LINE_HALO;
+                }
             }
             bool go = st == SG_LINE_ACTIVE;
             if (!go) ev = EV_STOP;
@@ -326,7 +355,10 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
                 }
                 ++step;
                 ++here;
-                write_vertex(P, line, step, c, f);
+                st_na(vp, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
+                st_na(vp + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
+                st_na(vp + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
+                vp += 3;
                 if (step >= horizon) {
                     ev = step >= P.max_steps ? EV_STOP : EV_PARK;
                     st = step >= P.max_steps ? SG_LINE_MAXSTEPS : st;
@@ -340,7 +372,8 @@ __global__ void __launch_bounds__(256) round_async_kernel(const __grid_constant_
                 }
             }
             stage = last ? 0 : stage + 1;
-            if (go) fetch();                      // the record of the next sample point q
+            const uint32_t next = cell_of();
+            if (go && next != held) fetch(next);  // the record of the next sample point q
         }
         if (__any_sync(SG_FULL_MASK, ev != EV_NONE)) {
             warp_append(ev == EV_APPEND, P.o, &P.ctrl->o_count, c, f, line, step);
