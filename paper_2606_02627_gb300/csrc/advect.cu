@@ -179,7 +179,10 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel
     // k1-k3 and ds: x and y as packed pairs, z alone
     f32x2 k1xy = 0, k2xy = 0, k3xy = 0, dsxy = 0;
     float k1z = 0.f, k2z = 0.f, k3z = 0.f, dsz = 0.f;
-    uint32_t line = 0, step = 0, here = 0, stage = 0;
+    uint32_t line = 0, step = 0, stage = 0;
+    // steps the lane may take before its step horizon or the round's step
+    // budget stops it: min(horizon - step, steps_per_round - steps this round)
+    int left = 0;
     uint32_t held = 0xffffffffu, wanted = 0;              // cell of the record in the slot / in flight
     BrickRef<DT> br;
     br.data = nullptr;
@@ -213,6 +216,7 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel
 
     while (true) {
         const unsigned need = __ballot_sync(SG_FULL_MASK, !active);
+        if (need == SG_FULL_MASK && drained) break;
         if (need && !drained) {
             const int leader = __ffs(need) - 1;
             uint32_t base = 0;
@@ -248,16 +252,15 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel
                         e2min = __fmul_ru(e, e);
                     }
                     vp = P.slab + ((long long)line * P.W + step + 1) * 3;
+                    left = step >= horizon ? 0 : (int)min(horizon - step, P.steps_per_round);
                     active = true;
-                    here = 0;
                     stage = 0;
                     fetch(cell_of());                // another brick: the slot's record is stale
                 }
             }
         }
-        if (__ballot_sync(SG_FULL_MASK, active) == 0) break;
         if (drained) {
-            if (drain_left == 0) here = P.steps_per_round;
+            if (drain_left == 0) left = 0;
             else --drain_left;
         }
         bool gave_up = false;
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel
         int ev = EV_NONE, st = SG_LINE_ACTIVE;
         float margin = INFINITY;
         bool run = active && !pending;
-        if (run && stage == 0) {
+        if (run && stage == 0 && left <= 0) {
             if (step >= horizon) {
                 if (step >= P.max_steps) {
                     ev = EV_STOP;
@@ -288,11 +291,10 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel
                 } else {
                     ev = EV_PARK;
                 }
-                run = false;
-            } else if (here >= P.steps_per_round) {
-                ev = EV_APPEND;
-                run = false;
+            } else {
+                ev = EV_APPEND;                   // the round's step budget is spent
             }
+            run = false;
         }
         if (run) {
             // one stage, the same instructions at every stage (the lanes of a
@@ -301,8 +303,8 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel
             Record<DT> R;
 #pragma unroll
             for (int k = 0; k < NCH; ++k) R.r[k] = slots[k * nthr + tid];
-            bool bad;
-            const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad);
+            bool bad_flag;                           // FX21: a corner's stored flag
+            const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad_flag);
             const f32x2 vxy = pk2(v.x, v.y);
             const float2 sq = upk2(mul2(vxy, vxy));
             const float s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
@@ -326,9 +328,13 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel
             const bool in_box = (unsigned)(q[0] - box_lo[0]) <= box_span[0] &&
                                 (unsigned)(q[1] - box_lo[1]) <= box_span[1] &&
                                 (unsigned)(q[2] - box_lo[2]) <= box_span[2];
-            if (bad || (stage == 0 && !(s2 >= e2min)) || !in_box) {
-                // the tests in full (rare): a non-finite sample, a speed that
-                // may be below eps, a point near the domain or brick boundary
+            // a non-finite component makes |v|^2 non-finite (the float formats)
+            const bool maybe_bad = (DT == SG_FX21) ? bad_flag : !(s2 < INFINITY);
+            if (maybe_bad || (stage == 0 && !(s2 >= e2min)) || !in_box) {
+                // the tests in full (rare): a sample that may not be finite, a
+                // speed that may be below eps, a point near the domain or
+                // brick boundary
+                const bool bad = (DT == SG_FX21) ? bad_flag : bad3(v);
                 float sp = sqrtf(s2);
                 if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
                 if (bad) {
@@ -354,21 +360,22 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel
                     f[a] = g[a];
                 }
                 ++step;
-                ++here;
+                --left;
                 st_na(vp, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
                 st_na(vp + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
                 st_na(vp + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
                 vp += 3;
-                if (step >= horizon) {
-                    ev = step >= P.max_steps ? EV_STOP : EV_PARK;
-                    st = step >= P.max_steps ? SG_LINE_MAXSTEPS : st;
+                const bool out = (unsigned)(c[0] - br.lo[0]) >= (unsigned)(br.hi[0] - br.lo[0]) ||
+                                 (unsigned)(c[1] - br.lo[1]) >= (unsigned)(br.hi[1] - br.lo[1]) ||
+                                 (unsigned)(c[2] - br.lo[2]) >= (unsigned)(br.hi[2] - br.lo[2]);
+                if (left <= 0 || out) {
                     go = false;
-                } else if (c[0] < br.lo[0] || c[0] >= br.hi[0] || c[1] < br.lo[1] || c[1] >= br.hi[1] ||
-                           c[2] < br.lo[2] || c[2] >= br.hi[2]) {
-                    ev = EV_APPEND;               // destinationID(new position) != this brick
-                    go = false;
-                } else {
-                    go = here < P.steps_per_round;   // else re-queued at the next pass, no fetch
+                    if (step >= horizon) {
+                        ev = step >= P.max_steps ? EV_STOP : EV_PARK;
+                        st = step >= P.max_steps ? SG_LINE_MAXSTEPS : st;
+                    } else if (out) {
+                        ev = EV_APPEND;           // destinationID(new position) != this brick
+                    }                             // else re-queued at the next pass, no fetch
                 }
             }
             stage = last ? 0 : stage + 1;

@@ -232,37 +232,45 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
     unsigned parity = 0, waited = 0;
     int c[3] = {0, 0, 0}, q[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};
-    float k1[3] = {0.f, 0.f, 0.f}, k2[3] = {0.f, 0.f, 0.f}, k3[3] = {0.f, 0.f, 0.f};
-    float ds[3] = {0.f, 0.f, 0.f};
-    uint32_t line = 0, step = 0, here = 0, stage = 0, r = 0, max_steps = 0;
+    // k1-k3 and ds: x and y as packed pairs, z alone
+    f32x2 k1xy = 0, k2xy = 0, k3xy = 0, dsxy = 0;
+    float k1z = 0.f, k2z = 0.f, k3z = 0.f, dsz = 0.f;
+    uint32_t line = 0, step = 0, stage = 0, r = 0, max_steps = 0;
+    int left = 0;                        // steps before max_steps or the round's step budget stops the lane
     uint32_t held = 0xffffffffu, wanted = 0;
     int dtype = SG_F32;
     float eps = 0.f;
-    float *vslab = nullptr;
+    float *vp = nullptr;                 // where the line's next vertex goes
     const ReqDev *R = P.reqs;
     BrickAny br;
     br.data = nullptr;
     br.scale = 1.0f;
     for (int a = 0; a < 3; ++a) br.lo[a] = br.hi[a] = 0;
+    // as in the tracer's kernel: a stage point in the box needs neither the
+    // EXIT nor the HALO test, and |v|^2 >= e2min means |v| >= eps
+    int box_lo[3] = {0, 0, 0};
+    unsigned box_span[3] = {0u, 0u, 0u};
+    float e2min = 0.f;
 
-    auto fetch = [&]() {
+    auto cell_of = [&]() {
         const DevField &F = R->F;
         const int sx = q[0] - br.lo[0] + 1, sy = q[1] - br.lo[1] + 1, sz = q[2] - br.lo[2] + 1;
-        const uint32_t cell = (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
-        if (cell != held) {
-            const int nch = dtype == SG_F32 ? Record<SG_F32>::chunks : Record<SG_F16>::chunks;
-            const uint4 *src = reinterpret_cast<const uint4 *>(br.data) + (long long)cell * nch;
-            for (int k = 0; k < nch; ++k) cp_async16(slot + k * nthr * 16u, src + k);
-            cp_async_arrive(bar);
-            held = 0xffffffffu;
-            wanted = cell;
-            pending = true;
-            waited = 0;
-        }
+        return (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
+    };
+    auto fetch = [&](uint32_t cell) {
+        const int nch = dtype == SG_F32 ? Record<SG_F32>::chunks : Record<SG_F16>::chunks;
+        const uint4 *src = reinterpret_cast<const uint4 *>(br.data) + (long long)cell * nch;
+        for (int k = 0; k < nch; ++k) cp_async16(slot + k * nthr * 16u, src + k);
+        cp_async_arrive(bar);
+        held = 0xffffffffu;
+        wanted = cell;
+        pending = true;
+        waited = 0;
     };
 
     while (true) {
         const unsigned need = __ballot_sync(SG_FULL_MASK, !active);
+        if (need == SG_FULL_MASK && drained) break;
         if (need && !drained) {
             const int leader = __ffs(need) - 1;
             uint32_t base = 0;
@@ -278,25 +286,38 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
                     dtype = R->dtype;
                     max_steps = R->max_steps;
                     eps = R->eps;
-                    vslab = P.slab + R->slab_base + (long long)(line - R->line_base) * R->W * 3;
+                    vp = P.slab + R->slab_base + ((long long)(line - R->line_base) * R->W + step + 1) * 3;
                     brick_any(R->F, dtype, c, br);
+                    float ds[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         ds[a] = dtype == SG_F32 ? R->dtc[a] : __fmul_rn(R->dtc[a], br.scale);
                         q[a] = c[a];
                         g[a] = f[a];
                     }
+                    dsxy = pk2(ds[0], ds[1]);
+                    dsz = ds[2];
+                    const DevField &F = R->F;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int lo = max(br.lo[a] - 1, 0);
+                        const int hi = min(br.lo[a] + F.S[a] - 3, F.nm1[a] - 1);
+                        box_lo[a] = hi >= lo ? lo : 0x7fffffff;   // empty: every point takes the full tests
+                        box_span[a] = hi >= lo ? (unsigned)(hi - lo) : 0u;
+                    }
+                    {
+                        const float e = dtype == SG_F32 ? eps : __fdiv_ru(eps, br.scale);
+                        e2min = __fmul_ru(e, e);
+                    }
+                    left = step >= max_steps ? 0 : (int)min(max_steps - step, P.steps_per_round);
                     active = true;
-                    here = 0;
                     stage = 0;
-                    held = 0xffffffffu;
-                    fetch();
+                    fetch(cell_of());
                 }
             }
         }
-        if (__ballot_sync(SG_FULL_MASK, active) == 0) break;
         if (drained) {
-            if (drain_left == 0) here = P.steps_per_round;
+            if (drain_left == 0) left = 0;
             else --drain_left;
         }
         bool gave_up = false;
@@ -317,46 +338,61 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
         int ev = EV_NONE, st = SG_LINE_ACTIVE;
         float margin = INFINITY;
         bool run = active && !pending;
-        if (run && stage == 0) {
+        if (run && stage == 0 && left <= 0) {
             if (step >= max_steps) {
                 ev = EV_STOP;
                 st = SG_LINE_MAXSTEPS;
-                run = false;
-            } else if (here >= P.steps_per_round) {
-                ev = EV_APPEND;
-                run = false;
+            } else {
+                ev = EV_APPEND;                   // the round's step budget is spent
             }
+            run = false;
         }
         if (run) {
             const DevField &F = R->F;
-            bool bad;
-            const float3 v = interp_slot(dtype, slots, nthr, tid, g[0], g[1], g[2], bad);
-            float sp = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
-            if (dtype != SG_F32) sp = __fmul_rn(sp, br.scale);
-            const float k[3] = {__fmul_rn(v.x, ds[0]), __fmul_rn(v.y, ds[1]), __fmul_rn(v.z, ds[2])};
+            bool bad_flag;                          // FX21: a corner's stored flag
+            const float3 v = interp_slot(dtype, slots, nthr, tid, g[0], g[1], g[2], bad_flag);
+            const f32x2 vxy = pk2(v.x, v.y);
+            const float2 sq = upk2(mul2(vxy, vxy));
+            const float s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
+            const f32x2 kxy = mul2(vxy, dsxy);
+            const float kz = __fmul_rn(v.z, dsz);
             const bool last = stage == 3;
             const float w = stage < 2 ? 0.5f : 1.0f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float fin =
-                    __fmul_rn(__fadd_rn(__fadd_rn(k1[a], k[a]), __fmul_rn(2.0f, __fadd_rn(k2[a], k3[a]))), 1.0f / 6.0f);
-                locate(f[a], last ? fin : w * k[a], c[a], q[a], g[a]);
-                k1[a] = stage == 0 ? k[a] : k1[a];
-                k2[a] = stage == 1 ? k[a] : k2[a];
-                k3[a] = stage == 2 ? k[a] : k3[a];
-            }
-            if (bad) {
-                st = SG_LINE_NANFIELD;
-            } else if (stage == 0 && sp < eps) {
-                margin = (eps - sp) / eps;
-                st = SG_LINE_STAGNANT;
-            } else if (!in_domain(F, q, g)) {
-                margin = out_dist(F, q, g);
-                st = SG_LINE_EXIT;
-            } else if (!last && ((unsigned)(q[0] - br.lo[0] + 1) > (unsigned)(F.S[0] - 2) ||
-                                 (unsigned)(q[1] - br.lo[1] + 1) > (unsigned)(F.S[1] - 2) ||
-                                 (unsigned)(q[2] - br.lo[2] + 1) > (unsigned)(F.S[2] - 2))) {
-                st = SG_LINE_HALO;
+            const float2 fin = upk2(mul2(add2(add2(k1xy, kxy), mul2(pk2(2.0f, 2.0f), add2(k2xy, k3xy))),
+                                         pk2(1.0f / 6.0f, 1.0f / 6.0f)));
+            const float finz = __fmul_rn(__fadd_rn(__fadd_rn(k1z, kz), __fmul_rn(2.0f, __fadd_rn(k2z, k3z))), 1.0f / 6.0f);
+            const float2 wk = upk2(mul2(pk2(w, w), kxy));
+            locate(f[0], last ? fin.x : wk.x, c[0], q[0], g[0]);
+            locate(f[1], last ? fin.y : wk.y, c[1], q[1], g[1]);
+            locate(f[2], last ? finz : w * kz, c[2], q[2], g[2]);
+            k1xy = stage == 0 ? kxy : k1xy;
+            k2xy = stage == 1 ? kxy : k2xy;
+            k3xy = stage == 2 ? kxy : k3xy;
+            k1z = stage == 0 ? kz : k1z;
+            k2z = stage == 1 ? kz : k2z;
+            k3z = stage == 2 ? kz : k3z;
+            const bool in_box = (unsigned)(q[0] - box_lo[0]) <= box_span[0] &&
+                                (unsigned)(q[1] - box_lo[1]) <= box_span[1] &&
+                                (unsigned)(q[2] - box_lo[2]) <= box_span[2];
+            const bool maybe_bad = dtype == SG_FX21 ? bad_flag : !(s2 < INFINITY);
+            if (maybe_bad || (stage == 0 && !(s2 >= e2min)) || !in_box) {
+                // the tests in full (rare)
+                const bool bad = dtype == SG_FX21 ? bad_flag : bad3(v);
+                float sp = sqrtf(s2);
+                if (dtype != SG_F32) sp = __fmul_rn(sp, br.scale);
+                if (bad) {
+                    st = SG_LINE_NANFIELD;
+                } else if (stage == 0 && sp < eps) {
+                    margin = (eps - sp) / eps;
+                    st = SG_LINE_STAGNANT;
+                } else if (!in_domain(F, q, g)) {
+                    margin = out_dist(F, q, g);
+                    st = SG_LINE_EXIT;
+                } else if (!last && ((unsigned)(q[0] - br.lo[0] + 1) > (unsigned)(F.S[0] - 2) ||
+                                     (unsigned)(q[1] - br.lo[1] + 1) > (unsigned)(F.S[1] - 2) ||
+                                     (unsigned)(q[2] - br.lo[2] + 1) > (unsigned)(F.S[2] - 2))) {
+                    st = SG_LINE_HALO;
+                }
             }
             bool go = st == SG_LINE_ACTIVE;
             if (!go) ev = EV_STOP;
@@ -367,25 +403,27 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
                     f[a] = g[a];
                 }
                 ++step;
-                ++here;
-                float *o = vslab + 3ll * step;
-                st_na(o, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
-                st_na(o + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
-                st_na(o + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
-                if (step >= max_steps) {
-                    ev = EV_STOP;
-                    st = SG_LINE_MAXSTEPS;
+                --left;
+                st_na(vp, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
+                st_na(vp + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
+                st_na(vp + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
+                vp += 3;
+                const bool out = (unsigned)(c[0] - br.lo[0]) >= (unsigned)(br.hi[0] - br.lo[0]) ||
+                                 (unsigned)(c[1] - br.lo[1]) >= (unsigned)(br.hi[1] - br.lo[1]) ||
+                                 (unsigned)(c[2] - br.lo[2]) >= (unsigned)(br.hi[2] - br.lo[2]);
+                if (left <= 0 || out) {
                     go = false;
-                } else if (c[0] < br.lo[0] || c[0] >= br.hi[0] || c[1] < br.lo[1] || c[1] >= br.hi[1] ||
-                           c[2] < br.lo[2] || c[2] >= br.hi[2]) {
-                    ev = EV_APPEND;
-                    go = false;
-                } else {
-                    go = here < P.steps_per_round;
+                    if (step >= max_steps) {
+                        ev = EV_STOP;
+                        st = SG_LINE_MAXSTEPS;
+                    } else if (out) {
+                        ev = EV_APPEND;
+                    }
                 }
             }
             stage = last ? 0 : stage + 1;
-            if (go) fetch();
+            const uint32_t next = cell_of();
+            if (go && next != held) fetch(next);
         }
         if (__any_sync(SG_FULL_MASK, ev != EV_NONE)) {
             warp_append(ev == EV_APPEND, P.o, &P.ctrl->o_count, c, f, line, step);
