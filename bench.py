@@ -562,7 +562,14 @@ def main():
     # headline: the chosen storage type and persistent kernel
     fld, tr = make(args.dtype, args.layout, args.kernel)
     if args.once:
+        # one whole step: field store, seeds, rounds, and the CSR gathered into device buffers
         one_step(fld, tr, None, None, None, seeds_dev)
+        nl, nv = tr.sizes(stream=stream)
+        o_off = torch.empty(nl + 1, dtype=torch.int64, device=dev)
+        o_vert = torch.empty((max(nv, 1), 3), dtype=torch.float32, device=dev)
+        o_st = torch.empty(max(nl, 1), dtype=torch.uint8, device=dev)
+        api.call("sg_tracer_get_lines", tr.h, None, None, api._ptr(o_off), api._ptr(o_vert), api._ptr(o_st), None,
+                 None, api._stream(stream))
         stream.synchronize()
         print(json.dumps({"once": True, "particle_steps": tr.total_steps(stream=stream),
                           "rounds": tr.check(stream=stream), "dtype": args.dtype, "layout": args.layout,

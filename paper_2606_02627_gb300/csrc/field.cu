@@ -236,6 +236,95 @@ __global__ void brick_store_cell8_kernel(StoreArgs A)
     }
 }
 
+// CELL8 with the source rows staged: a block builds a strip of STRIP rows of
+// cell records (fixed z, y from y0, all x) at a time.  It first copies the
+// sample rows those records read ((y0 .. y0 + STRIP) x (z, z + 1), S0
+// samples each, ghost shell included) into shared memory with coalesced
+// loads, then builds the records from there, one thread per 16-byte chunk,
+// with coalesced writes.  The same records as brick_store_cell8_kernel, bit
+// for bit.
+constexpr int STORE_STRIP = 6;
+
+template <int DT>
+__global__ void brick_store_cell8_staged_kernel(StoreArgs A)
+{
+    using T = typename Elem<DT>::T;
+    extern __shared__ float rowbuf[];               // [dz][dy 0..STRIP][3 * S0]
+    constexpr int CPR = Record<DT>::chunks;
+    const DevField &F = A.F;
+    const int b = A.brick0 + blockIdx.y;
+    const int bx = b % F.B[0], by = (b / F.B[0]) % F.B[1], bz = b / (F.B[0] * F.B[1]);
+    uint4 *brick = reinterpret_cast<uint4 *>(A.data + (long long)b * A.brick_bytes);
+    const float s = (DT == SG_F32) ? 1.0f : A.scales[b];
+    const int strips = (F.C[1] + STORE_STRIP - 1) / STORE_STRIP;
+    const int units = strips * F.C[2];
+    const int rowf = 3 * F.S[0];
+    const int row_chunks = F.C[0] * CPR;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const int cz = u / strips, y0 = (u - cz * strips) * STORE_STRIP;
+        const int ny = min(STORE_STRIP, F.C[1] - y0);    // record rows in this strip
+        const int nrows = ny + 1;                        // sample rows per z layer
+        __syncthreads();                                 // the previous strip's records are built
+        // sample row k = dy + nrows dz: one warp per row, the lanes along x
+        for (int k = warp; k < 2 * nrows; k += nwarps) {
+            const int dz = k >= nrows ? 1 : 0;
+            const int sy = y0 + k - dz * nrows, sz = cz + dz;
+            const float *row;
+            int x0 = 0, xhi = F.S[0] - 1;
+            if (A.src_mode == 1) {
+                row = A.src + 3ll * ((long long)sz * F.S[1] + sy) * F.S[0];
+            } else {
+                const int gy = clampi(by * F.n[1] - 1 + sy, 0, F.nm1[1]);
+                const int gz = clampi(bz * F.n[2] - 1 + sz, 0, F.nm1[2]);
+                row = A.src + 3ll * ((long long)gz * F.dims[1] + gy) * F.dims[0];
+                x0 = bx * F.n[0] - 1;
+                xhi = F.nm1[0];
+            }
+            float *d = rowbuf + k * rowf;
+            for (int sx = lane; sx < F.S[0]; sx += 32) {
+                const float *p = row + 3 * clampi(x0 + sx, 0, xhi);
+                d[3 * sx] = __ldg(p);
+                d[3 * sx + 1] = __ldg(p + 1);
+                d[3 * sx + 2] = __ldg(p + 2);
+            }
+        }
+        __syncthreads();
+        uint4 *dst = brick + ((long long)cz * F.C[1] + y0) * row_chunks;   // ny consecutive record rows
+        int ry = 0, jj = threadIdx.x;                    // record row and chunk within it of chunk j
+        while (jj >= row_chunks) {
+            jj -= row_chunks;
+            ++ry;
+        }
+        for (int j = threadIdx.x; j < ny * row_chunks; j += blockDim.x) {
+            const int cx = jj / CPR, jc = jj - cx * CPR;
+            auto smp = [&](int dx, int dy, int dz) {
+                return rowbuf + (dz * nrows + ry + dy) * rowf + 3 * (cx + dx);
+            };
+            uint4 out;
+            if constexpr (DT == SG_F32) {
+                // component a = jc / 2 of the four corners with x = jc % 2
+                const int a = jc >> 1, dx = jc & 1;
+                out = make_uint4(__float_as_uint(smp(dx, 0, 0)[a]), __float_as_uint(smp(dx, 0, 1)[a]),
+                                 __float_as_uint(smp(dx, 1, 0)[a]), __float_as_uint(smp(dx, 1, 1)[a]));
+            } else {
+                // corners 2 jc and 2 jc + 1: (0, dy, dz) and (1, dy, dz)
+                const int dy = jc & 1, dz = jc >> 1;
+                const float *p0 = smp(0, dy, dz), *p1 = smp(1, dy, dz);
+                const T e0 = encode_elem<DT>(p0[0], p0[1], p0[2], s);
+                const T e1 = encode_elem<DT>(p1[0], p1[1], p1[2], s);
+                out = make_uint4(e0.x, e0.y, e1.x, e1.y);
+            }
+            dst[j] = out;
+            jj += blockDim.x;
+            while (jj >= row_chunks) {
+                jj -= row_chunks;
+                ++ry;
+            }
+        }
+    }
+}
+
 // Plain copy for the global float3 layout.
 __global__ void global_copy_kernel(const float *__restrict__ src, float *__restrict__ dst, long long n)
 {
@@ -332,8 +421,13 @@ sg_status launch_brick_store(sg_field *f, int slot, const float *src, int src_mo
     SG_CUDA(cudaGetLastError());
     const int rows = A.F.C[1] * A.F.C[2];
     dim3 grid_rows((unsigned)std::min<long long>(rows, std::max(1, f->ctx->sm_count * 16 / nbr)), nbr);
+    const int strip_units = (A.F.C[1] + STORE_STRIP - 1) / STORE_STRIP * A.F.C[2];
+    dim3 grid_strips((unsigned)std::min<long long>(strip_units, std::max(1, f->ctx->sm_count * 8 / nbr)), nbr);
     const bool ok = with_dtype(d.dtype, [&](auto D) {
-        if (d.layout == SG_LAYOUT_CELL8)
+        const size_t staged = sizeof(float) * 3 * (size_t)A.F.S[0] * 2 * (STORE_STRIP + 1);   // sample rows of a strip
+        if (d.layout == SG_LAYOUT_CELL8 && staged <= 48 * 1024)
+            brick_store_cell8_staged_kernel<decltype(D)::value><<<grid_strips, block, staged, s>>>(A);
+        else if (d.layout == SG_LAYOUT_CELL8)
             brick_store_cell8_kernel<decltype(D)::value><<<grid_rows, block, 0, s>>>(A);
         else brick_store_kernel<decltype(D)::value><<<grid, block, 0, s>>>(A, d.layout);
     });
