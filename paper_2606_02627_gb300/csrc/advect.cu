@@ -153,7 +153,7 @@ constexpr unsigned COPY_WAIT_PASSES = 1u << 24;
 // rk4_bricked's, operation for operation, so both kernels produce the same
 // bits.
 template <int DT>
-__global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : 0) round_async_kernel(const __grid_constant__ LineParams P)
+__global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : (DT == SG_F32 ? 4 : 0)) round_async_kernel(const __grid_constant__ LineParams P)
 {
     constexpr int NCH = Record<DT>::chunks;
     extern __shared__ uint4 slots[];                       // [NCH][blockDim] chunks, then blockDim barriers

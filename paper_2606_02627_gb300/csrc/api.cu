@@ -313,11 +313,12 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
     t->block = p->block_size > 0 ? p->block_size : 256;
     // default resident threads per SM (measured on GB300): 512 for the kernels
     // that read every sample through L1, where more particles per SM thrash the
-    // L1 that holds their cell records; 768 for the decoupled-lane kernel,
-    // whose records sit in shared memory and which is bound by instruction
-    // issue instead
+    // L1 that holds their cell records; for the decoupled-lane kernel, whose
+    // records sit in shared memory and which is bound by instruction issue,
+    // as many as its registers allow: 1024 for FP32 (64 registers), 768 for
+    // the 8-byte formats
     const bool decoupled = p->kernel == SG_KERNEL_PERSISTENT && f->desc.layout == SG_LAYOUT_CELL8;
-    const int threads_per_sm = decoupled ? 768 : 512;
+    const int threads_per_sm = decoupled ? (f->desc.dtype == SG_F32 ? 1024 : 768) : 512;
     // round length (measured on GB300): the decoupled kernel gains from longer
     // rounds whose ends are cut short once the queue is empty
     if (t->p.steps_per_round <= 0) t->p.steps_per_round = decoupled ? 256 : 128;
