@@ -146,30 +146,36 @@ constexpr unsigned COPY_WAIT_PASSES = 1u << 24;
 // every sample some lane has just entered a cell whose record is not in L1.
 // Here each lane keeps the record of the cell of its current sample point in
 // its own shared-memory slot and runs one RK4 stage per pass of the warp's
-// loop.  When a stage point falls in another cell, the lane starts an
-// asynchronous copy of that record (cp.async through L1) into its slot,
+// loop.  When a stage point falls in another cell, the lane starts one bulk
+// copy of that record by the TMA engine (cp.async.bulk) into its slot,
 // completing on its own mbarrier, and sits out the passes until the copy has
-// landed while the other lanes go on.  The stage arithmetic is
+// landed while the other lanes go on.  A slot is the record plus 16 bytes of
+// padding (112 bytes for FP32, 80 for the 8-byte formats): with that stride
+// the 16-byte reads of eight consecutive lanes fall in eight different bank
+// groups.  The stage arithmetic is
 // rk4_bricked's, operation for operation, so both kernels produce the same
 // bits.
 template <int DT>
-__global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : (DT == SG_F32 ? 4 : 0)) round_async_kernel(const __grid_constant__ LineParams P)
+__global__ void __launch_bounds__(256, DT == SG_F32 ? 4 : (DT == SG_F16 ? 0 : 3)) round_async_kernel(const __grid_constant__ LineParams P)
 {
     constexpr int NCH = Record<DT>::chunks;
-    extern __shared__ uint4 slots[];                       // [NCH][blockDim] chunks, then blockDim barriers
+    constexpr unsigned SLOT = (NCH + 1) * 16;              // bytes per lane slot
+    extern __shared__ uint4 slots[];                       // [blockDim][SLOT bytes], then blockDim barriers
     const unsigned tid = threadIdx.x, nthr = blockDim.x;
     const unsigned lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + NCH * nthr) + tid);
-    const uint32_t slot = smem_addr(slots + tid);
+    const uint4 *my_slot = slots + tid * (SLOT / 16);
+    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + nthr * (SLOT / 16)) + tid);
+    const uint32_t slot = smem_addr(my_slot);
     mbar_init(bar, 1);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_init_fence();
     __syncwarp();
 
     const DevField &F = P.F;
     const uint32_t q_count = P.ctrl->q_count;
     const uint32_t horizon = P.ctrl->horizon;
     bool active = false, pending = false;
+    bool inflight = false;                                 // a copy may still land in the slot
     bool drained = q_count == 0;
     // four passes per step
     uint32_t drain_left = P.drain_steps >= 0x20000000u ? 0xffffffffu : P.drain_steps * 4u;
@@ -204,10 +210,8 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : (DT == SG_F32 ? 4 : 0
     };
     // copy the record of `cell` into the slot
     auto fetch = [&](uint32_t cell) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(br.data + (long long)cell * record_elems<DT>());
-#pragma unroll
-        for (int k = 0; k < NCH; ++k) cp_async16(slot + k * nthr * 16u, src + k);
-        cp_async_arrive(bar);
+        bulk_copy_arrive(slot, br.data + (long long)cell * record_elems<DT>(), NCH * 16u, bar);
+        inflight = true;
         held = 0xffffffffu;
         wanted = cell;
         pending = true;
@@ -269,6 +273,7 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : (DT == SG_F32 ? 4 : 0
                 held = wanted;
                 parity ^= 1u;
                 pending = false;
+                inflight = false;
             } else if (++waited >= COPY_WAIT_PASSES) {
                 // the particle is dropped and the call fails; the warp takes
                 // no other particle while this lane's barrier may still complete
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : (DT == SG_F32 ? 4 : 0
             // point P0 + w k (stages 0-2) or P' (stage 3)
             Record<DT> R;
 #pragma unroll
-            for (int k = 0; k < NCH; ++k) R.r[k] = slots[k * nthr + tid];
+            for (int k = 0; k < NCH; ++k) R.r[k] = my_slot[k];
             bool bad_flag;                           // FX21: a corner's stored flag
             const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad_flag);
             const f32x2 vxy = pk2(v.x, v.y);
@@ -395,7 +400,10 @@ __global__ void __launch_bounds__(256, DT == SG_FX21 ? 3 : (DT == SG_F32 ? 4 : 0
             if (ev != EV_NONE) active = false;
         }
     }
-    cp_async_wait_all();    // only after a copy wait ran out can one be in flight
+    // only after a copy wait ran out can one be in flight: wait for it once
+    // more, again with a limit, before the slot's memory is released
+    for (unsigned i = 0; inflight && i < COPY_WAIT_PASSES; ++i)
+        if (mbar_done(bar, parity)) inflight = false;
 }
 
 // ------------------------------------------------------------------ Listing 1: one launch per step
@@ -653,7 +661,7 @@ static bool use_async(int kernel, int layout) { return kernel == SG_KERNEL_PERSI
 template <int DT>
 static size_t async_smem(int block)
 {
-    return (size_t)block * (Record<DT>::chunks * 16 + 8);
+    return (size_t)block * ((Record<DT>::chunks + 1) * 16 + 8);
 }
 
 template <int DT, int LAYOUT>

@@ -368,6 +368,25 @@ __device__ __forceinline__ bool mbar_done(uint32_t bar, unsigned parity)
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// One bulk copy by the TMA engine of `bytes` from global to shared memory,
+// completing on the barrier: this thread's arrival on the barrier also adds
+// `bytes` to the transaction count of the phase, which the copy counts down
+// as it lands.  dst and src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_arrive(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Makes mbarrier initialisation visible to the TMA engine (the async proxy).
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // A cell record (CELL8 layout) as 16-byte chunks.  8-byte samples: 4 chunks,
 // chunk j holding corners 2j and 2j+1 (corner k = (x, y, z) = (k & 1,
 // k >> 1 & 1, k >> 2) from the cell's lower corner).  FP32: 6 chunks, one
