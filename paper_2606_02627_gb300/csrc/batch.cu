@@ -173,41 +173,41 @@ __global__ void __launch_bounds__(256) batch_round_kernel(const __grid_constant_
 
 // The same round with the lanes of a warp decoupled (CELL8 layout), as the
 // tracer's round_async_kernel: each lane keeps the cell record of its current
-// sample point in its own shared-memory slot (6 chunks of 16 B, enough for
-// FP32; the 8-byte formats use 4), fetches another with cp.async completing
-// on its own mbarrier, and runs one RK4 stage per pass; the storage type of
-// each lane's request selects the decode.  Stage arithmetic as rk4_bricked's.
-constexpr int BATCH_SLOT_CHUNKS = Record<SG_F32>::chunks;
+// sample point in its own shared-memory slot (an FP32 record of 6 chunks of
+// 16 B plus one chunk of padding: the 8-byte formats use 4 chunks of it),
+// fetches another with one TMA bulk copy completing on its own mbarrier, and
+// runs one RK4 stage per pass; the storage type of each lane's request
+// selects the decode.  Stage arithmetic as rk4_bricked's.
+constexpr int BATCH_SLOT_CHUNKS = Record<SG_F32>::chunks + 1;
 // Consecutive passes a lane may wait for one record copy (each pass takes at
 // least ~100 cycles: well over a second in all), as in the tracer's kernel.
 constexpr unsigned BATCH_COPY_WAIT_PASSES = 1u << 24;
 
-__device__ __forceinline__ float3 interp_slot(int dtype, const uint4 *slots, unsigned nthr, unsigned tid, float fx,
-                                              float fy, float fz, bool &bad)
+__device__ __forceinline__ float3 interp_slot(int dtype, const uint4 *slot, float fx, float fy, float fz, bool &bad)
 {
     switch (dtype) {
     case SG_BF16: {
         Record<SG_BF16> R;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) R.r[k] = slots[k * nthr + tid];
+        for (int k = 0; k < 4; ++k) R.r[k] = slot[k];
         return interp_record<SG_BF16>(R, fx, fy, fz, bad);
     }
     case SG_F16: {
         Record<SG_F16> R;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) R.r[k] = slots[k * nthr + tid];
+        for (int k = 0; k < 4; ++k) R.r[k] = slot[k];
         return interp_record<SG_F16>(R, fx, fy, fz, bad);
     }
     case SG_FX21: {
         Record<SG_FX21> R;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) R.r[k] = slots[k * nthr + tid];
+        for (int k = 0; k < 4; ++k) R.r[k] = slot[k];
         return interp_record<SG_FX21>(R, fx, fy, fz, bad);
     }
     default: {
         Record<SG_F32> R;
 #pragma unroll
-        for (int k = 0; k < Record<SG_F32>::chunks; ++k) R.r[k] = slots[k * nthr + tid];
+        for (int k = 0; k < Record<SG_F32>::chunks; ++k) R.r[k] = slot[k];
         return interp_record<SG_F32>(R, fx, fy, fz, bad);
     }
     }
@@ -215,18 +215,20 @@ __device__ __forceinline__ float3 interp_slot(int dtype, const uint4 *slots, uns
 
 __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant__ BatchParams P)
 {
-    extern __shared__ uint4 slots[];                       // [6][blockDim] chunks, then blockDim barriers
+    extern __shared__ uint4 slots[];                       // [blockDim][7 chunks], then blockDim barriers
     const unsigned tid = threadIdx.x, nthr = blockDim.x;
     const unsigned lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
+    const uint4 *my_slot = slots + tid * BATCH_SLOT_CHUNKS;
     const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + BATCH_SLOT_CHUNKS * nthr) + tid);
-    const uint32_t slot = smem_addr(slots + tid);
+    const uint32_t slot = smem_addr(my_slot);
     mbar_init(bar, 1);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_init_fence();
     __syncwarp();
 
     const uint32_t q_count = P.ctrl->q_count;
     bool active = false, pending = false;
+    bool inflight = false;                                 // a copy may still land in the slot
     bool drained = q_count == 0;
     uint32_t drain_left = P.drain_steps >= 0x20000000u ? 0xffffffffu : P.drain_steps * 4u;   // 4 passes a step
     unsigned parity = 0, waited = 0;
@@ -259,9 +261,8 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
     };
     auto fetch = [&](uint32_t cell) {
         const int nch = dtype == SG_F32 ? Record<SG_F32>::chunks : Record<SG_F16>::chunks;
-        const uint4 *src = reinterpret_cast<const uint4 *>(br.data) + (long long)cell * nch;
-        for (int k = 0; k < nch; ++k) cp_async16(slot + k * nthr * 16u, src + k);
-        cp_async_arrive(bar);
+        bulk_copy_arrive(slot, reinterpret_cast<const uint4 *>(br.data) + (long long)cell * nch, nch * 16u, bar);
+        inflight = true;
         held = 0xffffffffu;
         wanted = cell;
         pending = true;
@@ -326,6 +327,7 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
                 held = wanted;
                 parity ^= 1u;
                 pending = false;
+                inflight = false;
             } else if (++waited >= BATCH_COPY_WAIT_PASSES) {
                 atomicOr(&P.ctrl->err, CTRL_ERR_TIMEOUT);
                 active = false;
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
         if (run) {
             const DevField &F = R->F;
             bool bad_flag;                          // FX21: a corner's stored flag
-            const float3 v = interp_slot(dtype, slots, nthr, tid, g[0], g[1], g[2], bad_flag);
+            const float3 v = interp_slot(dtype, my_slot, g[0], g[1], g[2], bad_flag);
             const f32x2 vxy = pk2(v.x, v.y);
             const float2 sq = upk2(mul2(vxy, vxy));
             const float s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
@@ -436,7 +438,9 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
             if (ev != EV_NONE) active = false;
         }
     }
-    cp_async_wait_all();
+    // a copy left in flight after a wait ran out: wait for it once more, with a limit
+    for (unsigned i = 0; inflight && i < BATCH_COPY_WAIT_PASSES; ++i)
+        if (mbar_done(bar, parity)) inflight = false;
 }
 
 // Seeds of request r -> particles appended to the outgoing buffer, first
