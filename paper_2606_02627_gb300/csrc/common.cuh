@@ -341,19 +341,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
-// 16 bytes global -> shared through L1 (.ca: the line stays in L1).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-
-// The barrier's pending arrival completes when every earlier cp.async of this
-// thread has landed (the barrier expects one arrival per phase).
-__device__ __forceinline__ void cp_async_arrive(uint32_t bar)
-{
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-
 // Non-blocking: has the phase of the given parity completed?
 __device__ __forceinline__ bool mbar_done(uint32_t bar, unsigned parity)
 {
@@ -365,8 +352,6 @@ __device__ __forceinline__ bool mbar_done(uint32_t bar, unsigned parity)
         : "memory");
     return ok != 0u;
 }
-
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // One bulk copy by the TMA engine of `bytes` from global to shared memory,
 // completing on the barrier: this thread's arrival on the barrier also adds
