@@ -197,10 +197,11 @@ def reduce_over_ranks(ms: float, steps: int, dist, device):
     return float(t.item()), int(s.item())
 
 
-def cpu_oracle_rate(F_host, grid, seeds, dt, max_steps, seconds):
-    """Oracle particle-steps/s on the host cores over a bounded prefix of the seeds."""
+def cpu_oracle_rate(F_host, grid, seeds, dt, max_steps, seconds, nthreads=None):
+    """Oracle particle-steps/s on the host cores (all of them unless nthreads is given) over a bounded
+    prefix of the seeds."""
     import oracle
-    nthreads = oracle.default_threads()
+    nthreads = nthreads or oracle.default_threads()
     n0 = min(len(seeds), max(nthreads * 8, 64))
     t = time.perf_counter()
     L = oracle.trace_streamlines(F_host, grid.origin, grid.spacing, seeds[:n0], dt, max_steps, eps=1e-6,
@@ -636,6 +637,11 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {ns} of {args.seeds} seeds of the same workload on the FP32 field "
                          f"({steps} particle-steps in {secs:.1f} s)"}
+        # the same oracle on one core, over a shorter prefix
+        rate1, _, ns1, steps1, secs1 = cpu_oracle_rate(F_host, grid, seeds_np, dt, args.max_steps,
+                                                       args.cpu_seconds / 4, nthreads=1)
+        cpu["one_core"] = {"value": rate1, "unit": UNIT,
+                           "sample": f"first {ns1} seeds ({steps1} particle-steps in {secs1:.1f} s)"}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
