@@ -6,17 +6,21 @@
 // Newton's method, inside the cell's reference domain within tau).
 //
 // Layout (caller's workspace): one 256-byte record per cell, the eight
-// vertex positions (float4, the cell type in the first w) and the eight
-// vertex velocities (float4), so that testing and interpolating a cell reads
-// one contiguous record; the cells are stored in the order of the BVH's
-// leaves, each leaf a contiguous range; BVH nodes are 32 bytes (box with the
-// child / range in the w words).  The hierarchy is built on the host at
-// creation (median split of the cell centroids along the widest axis, at
-// most 4 cells per leaf).
+// vertex positions (float4, the cell type in the first w, the neighbours
+// across the cell's faces in the next six w words) and the eight vertex
+// velocities (float4), so that testing and interpolating a cell reads one
+// contiguous record; the cells are stored in the order of the BVH's leaves,
+// each leaf a contiguous range; BVH nodes are 32 bytes (box with the child /
+// range in the w words).  The hierarchy and the face neighbours (faces
+// matched by their vertex sets) are built on the host at creation (median
+// split of the cell centroids along the widest axis, at most 4 cells per
+// leaf).
 //
 // Tracing: one thread per seed to termination (Listing 1's RK4 in world
-// coordinates, positions in FP64, samples in FP32 relative to the cell), the
-// cell of the previous sample tried first, then the BVH.
+// coordinates, positions in FP64, samples in FP32 relative to the cell).  A
+// point is looked for in the cell of the previous sample first, then by
+// walking from it across the face whose parametric bound the point violates
+// most (a few cells at most), and only then in the BVH.
 #include <math.h>
 #include <string.h>
 
@@ -40,6 +44,21 @@ struct __align__(16) UNode {
 constexpr int UMESH_LEAF = 4;
 constexpr int UMESH_STACK = 64;
 constexpr int UMESH_NEWTON = 12;
+constexpr int UMESH_WALK = 6;                  // cells visited by a walk before the BVH takes over
+
+// Faces of each cell type (VTK vertex order), in the order of the parametric
+// bounds that exit_face reports: hexahedron a<0, a>1, b<0, b>1, c<0, c>1;
+// tetrahedron a<0, b<0, c<0, a+b+c>1; prism a<0, b<0, a+b>1, c<0, c>1;
+// pyramid a<0, a>1, b<0, b>1, c<0 (its apex has no face).  -1 pads a
+// triangle.
+struct UFaces {
+    int n;
+    int v[6][4];
+};
+static const UFaces UFACES_TET = {4, {{0, 2, 3, -1}, {0, 1, 3, -1}, {0, 1, 2, -1}, {1, 2, 3, -1}}};
+static const UFaces UFACES_PYR = {5, {{0, 3, 4, -1}, {1, 2, 4, -1}, {0, 1, 4, -1}, {2, 3, 4, -1}, {0, 1, 2, 3}}};
+static const UFaces UFACES_PRI = {5, {{0, 2, 5, 3}, {0, 1, 4, 3}, {1, 2, 5, 4}, {0, 1, 2, -1}, {3, 4, 5, -1}}};
+static const UFaces UFACES_HEX = {6, {{0, 3, 7, 4}, {1, 2, 6, 5}, {0, 1, 5, 4}, {3, 2, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}}};
 
 }  // namespace sg
 
@@ -154,7 +173,10 @@ __device__ float ucell_param(const UCell &C, double3 pw, float r[3], bool warm =
         r[0] -= d0;
         r[1] -= d1;
         r[2] -= d2;
-        if (fabsf(d0) + fabsf(d1) + fabsf(d2) < 1e-7f) break;
+        // converged to well inside the containment tolerance (FP32 rounding
+        // keeps the update near 1e-7 for coordinates of order one, so a
+        // tighter test would run every iteration)
+        if (fabsf(d0) + fabsf(d1) + fabsf(d2) < 3e-6f) break;
         if (fabsf(r[0]) + fabsf(r[1]) + fabsf(r[2]) > 1e6f) break;
     }
     // a parametric point counts only if it maps back onto p (Newton converged)
@@ -195,12 +217,52 @@ struct UMeshView {
     float tau;
 };
 
-// The stored cell containing p (hint first, then the hierarchy), or -1.  r
-// holds the parametric coordinates of the previous sample in the hint cell
-// (the warm start) and receives those of p.
+// The face (in UFaces order) whose parametric bound the point r violates
+// most, or -1 (a pyramid's apex).
+__device__ __forceinline__ int exit_face(int type, const float r[3])
+{
+    const float a = r[0], b = r[1], c = r[2];
+    float best;
+    int f;
+    if (type == 4) {
+        best = -a, f = 0;
+        if (-b > best) best = -b, f = 1;
+        if (-c > best) best = -c, f = 2;
+        if (a + b + c - 1.f > best) f = 3;
+        return f;
+    }
+    if (type == 6) {
+        best = -a, f = 0;
+        if (-b > best) best = -b, f = 1;
+        if (a + b - 1.f > best) best = a + b - 1.f, f = 2;
+        if (-c > best) best = -c, f = 3;
+        if (c - 1.f > best) f = 4;
+        return f;
+    }
+    best = -a, f = 0;
+    if (a - 1.f > best) best = a - 1.f, f = 1;
+    if (-b > best) best = -b, f = 2;
+    if (b - 1.f > best) best = b - 1.f, f = 3;
+    if (-c > best) best = -c, f = 4;
+    if (c - 1.f > best) f = type == 8 ? 5 : -1;
+    return f;
+}
+
+// The stored cell containing p, or -1: the hint cell, then a walk across the
+// faces from it, then the hierarchy.  r holds the parametric coordinates of
+// the previous sample in the hint cell (the warm start) and receives those
+// of p.
 __device__ long long ulocate(const UMeshView &M, double3 pw, long long hint, float r[3], bool warm = false)
 {
-    if (hint >= 0 && ucell_param(M.cells[hint], pw, r, warm) <= M.tau) return hint;
+    for (int hop = 0; hint >= 0 && hop < UMESH_WALK; ++hop) {
+        const UCell &C = M.cells[hint];
+        const float viol = ucell_param(C, pw, r, warm);
+        if (viol <= M.tau) return hint;
+        if (!(viol < INFINITY)) break;             // no parametric solution: the hierarchy decides
+        const int f = exit_face(__float_as_int(C.x[0].w), r);
+        hint = f >= 0 ? __float_as_int(C.x[1 + f].w) : -1;
+        warm = false;
+    }
     const float3 p = make_float3((float)pw.x, (float)pw.y, (float)pw.z);
     if (M.n_cells == 0) return -1;
     int stack[UMESH_STACK];
@@ -474,6 +536,47 @@ extern "C" sg_status sg_umesh_create(sg_context *ctx, const float *vertices, con
     }
     std::vector<UCell> sorted((size_t)n_cells);
     for (int64_t k = 0; k < n_cells; ++k) sorted[(size_t)k] = rec[(size_t)order[(size_t)k]];
+    // face neighbours: faces matched by their sorted vertex ids; stored as
+    // the neighbour's position in the stored order (-1: on the boundary)
+    {
+        std::vector<int32_t> pos((size_t)n_cells);
+        for (int64_t k = 0; k < n_cells; ++k) pos[(size_t)order[(size_t)k]] = (int32_t)k;
+        struct FaceKey {
+            uint64_t k0, k1;
+            int32_t cell;
+            int32_t slot;
+        };
+        std::vector<FaceKey> faces;
+        faces.reserve((size_t)n_cells * 6);
+        for (int64_t c = 0; c < n_cells; ++c) {
+            const int type = cell_types[c];
+            const UFaces &F = type == 4 ? UFACES_TET : type == 5 ? UFACES_PYR : type == 6 ? UFACES_PRI : UFACES_HEX;
+            for (int f = 0; f < F.n; ++f) {
+                uint32_t v[4];
+                for (int i = 0; i < 4; ++i)
+                    v[i] = F.v[f][i] < 0 ? 0xffffffffu : (uint32_t)cell_vertices[cell_offsets[c] + F.v[f][i]];
+                std::sort(v, v + 4);
+                faces.push_back({((uint64_t)v[0] << 32) | v[1], ((uint64_t)v[2] << 32) | v[3], (int32_t)c, f});
+            }
+        }
+        std::sort(faces.begin(), faces.end(), [](const FaceKey &p, const FaceKey &q) {
+            return p.k0 != q.k0 ? p.k0 < q.k0 : (p.k1 != q.k1 ? p.k1 < q.k1 : p.cell < q.cell);
+        });
+        for (int64_t k = 0; k < n_cells; ++k)
+            for (int f = 0; f < 6; ++f) {
+                const int none = -1;
+                memcpy(&sorted[(size_t)k].x[1 + f].w, &none, 4);
+            }
+        for (size_t i = 0; i + 1 < faces.size(); ++i) {
+            const FaceKey &p = faces[i], &q = faces[i + 1];
+            if (p.k0 != q.k0 || p.k1 != q.k1) continue;
+            if (i + 2 < faces.size() && faces[i + 2].k0 == p.k0 && faces[i + 2].k1 == p.k1) continue;   // not manifold
+            if (i > 0 && faces[i - 1].k0 == p.k0 && faces[i - 1].k1 == p.k1) continue;
+            const int32_t a = pos[(size_t)p.cell], b = pos[(size_t)q.cell];
+            memcpy(&sorted[(size_t)a].x[1 + p.slot].w, &b, 4);
+            memcpy(&sorted[(size_t)b].x[1 + q.slot].w, &a, 4);
+        }
+    }
     SG_CUDA(cudaSetDevice(ctx->device));
     Carve cv{(char *)workspace, 0, 0};
     UCell *dcells = (UCell *)cv.take(sizeof(UCell) * (size_t)n_cells);
