@@ -130,8 +130,10 @@ __device__ __forceinline__ float uviolation(int type, const float r[3])
 // precision relative to the cell's size; returns how far outside the
 // reference domain they lie (<= tau: inside).
 // warm: r already holds a guess (the previous sample's coordinates in this
-// cell), else Newton starts from the cell's centre.
-__device__ float ucell_param(const UCell &C, double3 pw, float r[3], bool warm = false)
+// cell), else Newton starts from the cell's centre.  Not inlined: one copy
+// serves every call site, and its loops run over the 8 vertex slots
+// unrolled, so the shape functions stay in registers.
+__device__ __noinline__ float ucell_param(const UCell &C, double3 pw, float r[3], bool warm = false)
 {
     const int type = __float_as_int(C.x[0].w);
     const float4 X0 = C.x[0];
@@ -147,7 +149,9 @@ __device__ float ucell_param(const UCell &C, double3 pw, float r[3], bool warm =
         ushape(type, r[0], r[1], r[2], N, dN);
         float x0 = -p.x, x1 = -p.y, x2 = -p.z;
         float J[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        for (int i = 0; i < type; ++i) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i >= type) break;
             const float4 Xw = C.x[i];
             const float3 X = make_float3(Xw.x - X0.x, Xw.y - X0.y, Xw.z - X0.z);
             x0 = fmaf(N[i], X.x, x0);
@@ -183,7 +187,9 @@ __device__ float ucell_param(const UCell &C, double3 pw, float r[3], bool warm =
     float N[8], dN[8][3];
     ushape(type, r[0], r[1], r[2], N, dN);
     float x0 = -p.x, x1 = -p.y, x2 = -p.z, ext = 0.f;
-    for (int i = 0; i < type; ++i) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i >= type) break;
         const float4 Xw = C.x[i];
         const float3 X = make_float3(Xw.x - X0.x, Xw.y - X0.y, Xw.z - X0.z);
         x0 = fmaf(N[i], X.x, x0);
@@ -201,7 +207,9 @@ __device__ float3 ucell_value(const UCell &C, const float r[3])
     float N[8], dN[8][3];
     ushape(type, r[0], r[1], r[2], N, dN);
     float3 v = make_float3(0.f, 0.f, 0.f);
-    for (int i = 0; i < type; ++i) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i >= type) break;
         const float4 V = C.v[i];
         v.x = fmaf(N[i], V.x, v.x);
         v.y = fmaf(N[i], V.y, v.y);
