@@ -323,18 +323,20 @@ struct UTraceArgs {
 
 // One RK4 step (Listing 1) in world coordinates; returns the status
 // (SG_LINE_ACTIVE on success with pn set).  Positions are kept in FP64 (a
-// handful of additions per step); the samples are FP32.
-__device__ int urk4(const UMeshView &M, double3 p, float dt, float eps, long long &hint, float rp[3], double3 &pn,
-                    float &margin)
+// handful of additions per step); the samples are FP32.  P0 comes located:
+// its cell (hint), its coordinates there (rp) and its velocity (v0), from
+// the previous step's locate of its new position; on success they are
+// replaced by those of pn.
+__device__ int urk4(const UMeshView &M, double3 p, float dt, float eps, long long &hint, float rp[3], float3 &v0,
+                    double3 &pn, float &margin)
 {
-    // rp: P0's coordinates in the hint cell (from the previous step's last locate)
-    float r[3] = {rp[0], rp[1], rp[2]}, r0[3];
-    long long c = ulocate(M, p, hint, r, true);
-    const long long c0 = c;
-    r0[0] = r[0];
-    r0[1] = r[1];
-    r0[2] = r[2];
-    float3 v = ucell_value(M.cells[c], r);
+    float r[3], r0[3];
+    const long long c0 = hint;
+    long long c = c0;
+    r0[0] = rp[0];
+    r0[1] = rp[1];
+    r0[2] = rp[2];
+    float3 v = v0;
     if (bad3(v)) return SG_LINE_NANFIELD;
     const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
     if (sp < eps) {
@@ -377,6 +379,7 @@ __device__ int urk4(const UMeshView &M, double3 p, float dt, float eps, long lon
     rp[0] = r[0];
     rp[1] = r[1];
     rp[2] = r[2];
+    v0 = ucell_value(M.cells[c], r);
     return SG_LINE_ACTIVE;
 }
 
@@ -397,11 +400,12 @@ __global__ void __launch_bounds__(256) umesh_trace_kernel(UMeshView M, UTraceArg
         out[0] = A.seeds[3 * i];
         out[1] = A.seeds[3 * i + 1];
         out[2] = A.seeds[3 * i + 2];
+        float3 v0 = ucell_value(M.cells[hint], r);
         uint32_t step = 0;
         int st = SG_LINE_MAXSTEPS;
         while (step < A.max_steps) {
             double3 pn;
-            const int s = urk4(M, p, A.dt, A.eps, hint, r, pn, margin);
+            const int s = urk4(M, p, A.dt, A.eps, hint, r, v0, pn, margin);
             if (s != SG_LINE_ACTIVE) {
                 st = s;
                 break;
