@@ -240,7 +240,13 @@ typedef struct {
     int32_t steps_per_round; /* steps a particle may take in one round before it is
                                 re-queued in its own brick (0 = default: 256 for the
                                 decoupled-lane kernel, 128 otherwise)               */
-    int32_t max_rounds;    /* round cap of one trace / step call                     */
+    int32_t max_rounds;    /* round cap of one trace / step call (0 = max_steps + 2,
+                              which only a fault can reach).  A call stopped by it
+                              returns (or its sg_tracer_check reports)
+                              SG_ERR_ROUND_LIMIT; its lines stay consistent: every
+                              particle left keeps the vertices written so far
+                              (status SG_LINE_ACTIVE, length = steps + 1) and the
+                              next trace / step call continues it             */
     int32_t drain_steps;   /* once a warp finds the round's queue empty, its lanes take
                               at most this many more steps before re-queueing their
                               particles for the next round: shortens the end of a

@@ -466,73 +466,121 @@ __global__ void __launch_bounds__(256) per_step_kernel(const __grid_constant__ L
 
 // ------------------------------------------------------------------ per-seed kernel (global float3 field)
 
-// Trilinear sample of the global float3 AoS array at index point p (inside
-// the domain); the lower cell index is clamped to dims-2.
-__device__ __forceinline__ float3 sample_global(const float *__restrict__ Fg, const DevField &F, float px, float py,
-                                                float pz)
+// Trilinear sample of the global float3 AoS array at cell c, fraction f (a
+// point inside the domain).  On the upper face (c = dims-1, f = 0) the upper
+// corner repeats the last sample, as a brick's clamped ghost layer does, so the
+// sample is that sample exactly.
+__device__ __forceinline__ float3 sample_global(const float *__restrict__ Fg, const DevField &F, const int c[3],
+                                                const float f[3])
 {
-    int cx = min((int)floorf(px), F.nm1[0] - 1);
-    int cy = min((int)floorf(py), F.nm1[1] - 1);
-    int cz = min((int)floorf(pz), F.nm1[2] - 1);
-    const float fx = px - (float)cx, fy = py - (float)cy, fz = pz - (float)cz;
-    const long long sx = 3, sy = 3ll * F.dims[0], sz = 3ll * F.dims[0] * F.dims[1];
-    const float *b = Fg + (long long)cz * sz + (long long)cy * sy + (long long)cx * sx;
-    float3 r;
-    float v[8];
+    const long long sy = 3ll * F.dims[0], sz = sy * F.dims[1];
+    const long long x0 = 3ll * c[0], x1 = 3ll * min(c[0] + 1, F.nm1[0]);
+    const long long y0 = sy * c[1], y1 = sy * min(c[1] + 1, F.nm1[1]);
+    const long long z0 = sz * c[2], z1 = sz * min(c[2] + 1, F.nm1[2]);
+    float r[3];
 #pragma unroll
     for (int comp = 0; comp < 3; ++comp) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            v[k] = __ldg(b + comp + ((k & 1) ? sx : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
-        const float val = lerpf(lerpf(lerpf(v[0], v[1], fx), lerpf(v[2], v[3], fx), fy),
-                                lerpf(lerpf(v[4], v[5], fx), lerpf(v[6], v[7], fx), fy), fz);
-        if (comp == 0) r.x = val;
-        else if (comp == 1) r.y = val;
-        else r.z = val;
+        const float *b = Fg + comp;
+        const float v000 = __ldg(b + z0 + y0 + x0), v100 = __ldg(b + z0 + y0 + x1);
+        const float v010 = __ldg(b + z0 + y1 + x0), v110 = __ldg(b + z0 + y1 + x1);
+        const float v001 = __ldg(b + z1 + y0 + x0), v101 = __ldg(b + z1 + y0 + x1);
+        const float v011 = __ldg(b + z1 + y1 + x0), v111 = __ldg(b + z1 + y1 + x1);
+        r[comp] = lerpf(lerpf(lerpf(v000, v100, f[0]), lerpf(v010, v110, f[0]), f[1]),
+                        lerpf(lerpf(v001, v101, f[0]), lerpf(v011, v111, f[0]), f[1]), f[2]);
     }
-    return r;
+    return make_float3(r[0], r[1], r[2]);
 }
 
-__device__ __forceinline__ bool in_box(const DevField &F, float x, float y, float z)
+// One RK4 step (Listing 1) on the global array, with rk4_bricked's operations
+// in the same order: stage points are formed relative to the particle's cell,
+// so the position keeps ~2^-24 cells of rounding anywhere in the grid.
+__device__ __forceinline__ int rk4_global(const float *__restrict__ Fg, const DevField &F, const float ds[3], float eps,
+                                          int c[3], float f[3], float &margin)
 {
-    return x >= 0.f && x <= (float)F.nm1[0] && y >= 0.f && y <= (float)F.nm1[1] && z >= 0.f && z <= (float)F.nm1[2];
-}
-
-__device__ __forceinline__ float box_out(const DevField &F, float x, float y, float z)
-{
-    float d = 0.f;
-    d = fmaxf(d, -x);
-    d = fmaxf(d, x - (float)F.nm1[0]);
-    d = fmaxf(d, -y);
-    d = fmaxf(d, y - (float)F.nm1[1]);
-    d = fmaxf(d, -z);
-    d = fmaxf(d, z - (float)F.nm1[2]);
-    return d;
+    float3 v = sample_global(Fg, F, c, f);
+    if (bad3(v)) return SG_LINE_NANFIELD;
+    const float sp = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z)));
+    if (sp < eps) {
+        margin = (eps - sp) / eps;
+        return SG_LINE_STAGNANT;
+    }
+    float k[4][3];
+    const float w[3] = {0.5f, 0.5f, 1.0f};     // P1, P2 = P0 + k/2; P3 = P0 + k3
+    int q[3];
+    float g[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        k[s][0] = __fmul_rn(v.x, ds[0]);
+        k[s][1] = __fmul_rn(v.y, ds[1]);
+        k[s][2] = __fmul_rn(v.z, ds[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) locate(f[a], w[s] * k[s][a], c[a], q[a], g[a]);
+        if (!in_domain(F, q, g)) {
+            margin = out_dist(F, q, g);
+            return SG_LINE_EXIT;
+        }
+        v = sample_global(Fg, F, q, g);
+        if (bad3(v)) return SG_LINE_NANFIELD;
+    }
+    k[3][0] = __fmul_rn(v.x, ds[0]);
+    k[3][1] = __fmul_rn(v.y, ds[1]);
+    k[3][2] = __fmul_rn(v.z, ds[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d = __fmul_rn(__fadd_rn(__fadd_rn(k[0][a], k[3][a]), __fmul_rn(2.0f, __fadd_rn(k[1][a], k[2][a]))),
+                                  1.0f / 6.0f);
+        locate(f[a], d, c[a], q[a], g[a]);
+    }
+    if (!in_domain(F, q, g)) {
+        margin = out_dist(F, q, g);
+        return SG_LINE_EXIT;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        c[a] = q[a];
+        f[a] = g[a];
+    }
+    return SG_LINE_ACTIVE;
 }
 
 // A grid-stride loop over the seeds: the grid sets how many seeds are in
 // flight per SM (as for the persistent kernel), each thread traces its seeds
-// one after the other.
+// one after the other to termination.
 __global__ void __launch_bounds__(256) per_seed_kernel(const __grid_constant__ LineParams P)
 {
     const float *Fg = reinterpret_cast<const float *>(P.F.data);
     const DevField &F = P.F;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n_lines;
          i += (long long)gridDim.x * blockDim.x) {
-        // index-space seed, converted in double precision
+        // seed to cell + fraction, converted in double precision (as the upload)
         const float *sd = P.seeds + 3 * seed_of(P, i);
-        float dtc[3];
-        line_dtc(P, i, dtc);
-        const double sx = ((double)sd[0] - P.origin_d[0]) / P.spacing_d[0];
-        const double sy = ((double)sd[1] - P.origin_d[1]) / P.spacing_d[1];
-        const double sz = ((double)sd[2] - P.origin_d[2]) / P.spacing_d[2];
-        if (!(sx >= 0.0 && sx <= F.nm1[0] && sy >= 0.0 && sy <= F.nm1[1] && sz >= 0.0 && sz <= F.nm1[2])) {
+        float ds[3];
+        line_dtc(P, i, ds);
+        double p[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            p[a] = ((double)sd[a] - P.origin_d[a]) / P.spacing_d[a];
+            inside = inside && (p[a] >= 0.0 && p[a] <= (double)F.nm1[a]);
+        }
+        if (!inside) {
             P.line_len[i] = 0;
             P.line_status[i] = SG_LINE_OUT;
             P.line_margin[i] = INFINITY;
             continue;
         }
-        float px = (float)sx, py = (float)sy, pz = (float)sz;
+        int c[3];
+        float f[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double fl = floor(p[a]);
+            c[a] = (int)fl;
+            f[a] = (float)(p[a] - fl);
+            if (f[a] >= 1.0f) {
+                f[a] = 0.0f;
+                c[a] += 1;
+            }
+        }
         float *out = P.slab + (long long)i * P.W * 3;
         out[0] = sd[0];
         out[1] = sd[1];
@@ -541,36 +589,16 @@ __global__ void __launch_bounds__(256) per_seed_kernel(const __grid_constant__ L
         int st = SG_LINE_MAXSTEPS;
         float margin = INFINITY;
         while (step < P.max_steps) {
-            float3 v = sample_global(Fg, F, px, py, pz);
-            if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-            const float sp = sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
-            if (sp < P.eps) { st = SG_LINE_STAGNANT; margin = (P.eps - sp) / P.eps; break; }
-            const float k1x = v.x * dtc[0], k1y = v.y * dtc[1], k1z = v.z * dtc[2];
-            float qx = px + 0.5f * k1x, qy = py + 0.5f * k1y, qz = pz + 0.5f * k1z;
-            if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
-            v = sample_global(Fg, F, qx, qy, qz);
-            if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-            const float k2x = v.x * dtc[0], k2y = v.y * dtc[1], k2z = v.z * dtc[2];
-            qx = px + 0.5f * k2x; qy = py + 0.5f * k2y; qz = pz + 0.5f * k2z;
-            if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
-            v = sample_global(Fg, F, qx, qy, qz);
-            if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-            const float k3x = v.x * dtc[0], k3y = v.y * dtc[1], k3z = v.z * dtc[2];
-            qx = px + k3x; qy = py + k3y; qz = pz + k3z;
-            if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
-            v = sample_global(Fg, F, qx, qy, qz);
-            if (bad3(v)) { st = SG_LINE_NANFIELD; break; }
-            const float k4x = v.x * dtc[0], k4y = v.y * dtc[1], k4z = v.z * dtc[2];
-            qx = px + (k1x + k4x + 2.0f * (k2x + k3x)) * (1.0f / 6.0f);
-            qy = py + (k1y + k4y + 2.0f * (k2y + k3y)) * (1.0f / 6.0f);
-            qz = pz + (k1z + k4z + 2.0f * (k2z + k3z)) * (1.0f / 6.0f);
-            if (!in_box(F, qx, qy, qz)) { st = SG_LINE_EXIT; margin = box_out(F, qx, qy, qz); break; }
-            px = qx; py = qy; pz = qz;
+            const int r = rk4_global(Fg, F, ds, P.eps, c, f, margin);
+            if (r != SG_LINE_ACTIVE) {
+                st = r;
+                break;
+            }
             ++step;
             float *o = out + 3ll * step;
-            st_na(o, fmaf(F.spacing[0], px, F.origin[0]));
-            st_na(o + 1, fmaf(F.spacing[1], py, F.origin[1]));
-            st_na(o + 2, fmaf(F.spacing[2], pz, F.origin[2]));
+            st_na(o, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
+            st_na(o + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
+            st_na(o + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
         }
         P.line_len[i] = step + 1;
         P.line_status[i] = stop_code(P, st, margin);

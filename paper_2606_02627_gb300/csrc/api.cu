@@ -440,6 +440,7 @@ static sg_status build_graph(sg_tracer *t)
             if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &cond, nullptr, 1, cudaStreamSetCaptureDependencies);
             if (e != cudaSuccess) st = cuda_error(e, "conditional node");
         }
+        if (st == SG_OK) st = launch_park_rest(t, cs);
         cudaGraph_t g2 = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &g2);
         if (st == SG_OK && e2 != cudaSuccess) st = cuda_error(e2, "cudaStreamEndCapture");
@@ -477,9 +478,12 @@ static sg_status run_call(sg_tracer *t, uint32_t horizon, uint32_t n_steps, cuda
         sg_status st = build_graph(t);
         if (st) return st;
     }
-    // every round advances each remaining particle by at least one step, so
-    // n_steps + 1 rounds finish a call; the cap only guards against a fault
-    uint64_t cap = (uint64_t)n_steps + 2;
+    // every round advances each remaining particle by at least one step, and
+    // no particle starts a call below step 0 (a call that the round cap
+    // stopped leaves particles behind the horizon), so horizon + 2 rounds
+    // finish a call; this cap only guards against a fault
+    (void)n_steps;
+    uint64_t cap = (uint64_t)horizon + 2;
     if (t->p.max_rounds > 0 && (uint64_t)t->p.max_rounds < cap) cap = (uint64_t)t->p.max_rounds;
     if (cap > 0xffffffffull) cap = 0xffffffffull;
     sg_status st = launch_prepare_call(t, horizon, (uint32_t)cap, s);
@@ -548,8 +552,10 @@ extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int3
         const uint32_t target = (uint32_t)t->p.max_steps;
         const uint32_t n = target > t->horizon ? target - t->horizon : 0;
         t->horizon = target;
-        uint64_t cap = (uint64_t)n + 2;
+        (void)n;
+        uint64_t cap = (uint64_t)target + 2;
         if (t->p.max_rounds > 0 && (uint64_t)t->p.max_rounds < cap) cap = (uint64_t)t->p.max_rounds;
+        if (cap > 0xffffffffull) cap = 0xffffffffull;
         st = launch_prepare_call(t, target, (uint32_t)cap, s);
         if (st == SG_OK) st = launch_bin(t, t->park, &t->ctrl->p_count, s, false, 0ull, 0);
         Ctrl c;
@@ -577,6 +583,7 @@ extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int3
             ++n_launch;
         }
         t->scanned = false;
+        if (st == SG_OK) st = launch_park_rest(t, s);
         if (st == SG_OK && c.q_count > 0) {
             set_error("the round cap stopped the trace with particles left");
             st = SG_ERR_ROUND_LIMIT;

@@ -135,6 +135,39 @@ __global__ void ctrl_kernel(Ctrl *ctrl, uint32_t *src_count, int mode, cudaGraph
     if (use_graph) cudaGraphSetConditional(h, (more && !capped) ? 1u : 0u);
 }
 
+// After the round loop of a call: if the round cap stopped it with particles
+// left, those particles (the next round's queue) are parked for the next call,
+// and each one's line length is brought up to the vertices written so far, so
+// that the partial lines read back consistently and a later trace() or step()
+// continues them from where they stopped.  One block: the counters move once
+// every record has been copied.
+__global__ void __launch_bounds__(1024) park_rest_kernel(Ctrl *ctrl, const Particle *q, Particle *park,
+                                                         uint32_t *line_len)
+{
+    if (!(ctrl->err & CTRL_ERR_ROUND_LIMIT)) return;
+    const uint32_t n = ctrl->q_count, base = ctrl->p_count;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int4 *s = reinterpret_cast<const int4 *>(q + i);
+        const int4 r0 = s[0], r1 = s[1];
+        int4 *d = reinterpret_cast<int4 *>(park + base + i);
+        d[0] = r0;
+        d[1] = r1;
+        line_len[(uint32_t)r0.w] = (uint32_t)r1.w + 1u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctrl->p_count = base + n;
+        ctrl->q_count = 0;
+    }
+}
+
+sg_status launch_park_rest(sg_tracer *t, cudaStream_t s)
+{
+    park_rest_kernel<<<1, 1024, 0, s>>>(t->ctrl, t->q, t->park, t->line_len);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
+}
+
 __global__ void prepare_kernel(Ctrl *ctrl, uint32_t horizon, uint32_t max_rounds)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;

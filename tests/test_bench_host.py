@@ -43,10 +43,14 @@ def test_hash_sees_kernel_changes(fake_root):
 
 
 def test_traffic_needs_matching_hash(fake_root):
-    # the committed summaries match the committed sources
-    assert bench.traffic_per_step("f32", "async") is not None
-    assert bench.traffic_per_step("fx21", "async") is not None
-    p = fake_root / "paper_2606_02627_gb300" / "csrc" / "advect.cu"
-    p.write_text(p.read_text() + "\n// edit\n")
+    # a summary carrying the hash of the sources it was captured on is read;
+    # once a kernel source changes, the figure no longer applies
+    p = fake_root / "profiles" / "round_async_f32_traffic.txt"
+    p.write_text("# capture notes\n"
+                 f"kernel_source_hash: {bench.kernel_hash()}\n"
+                 "dram_bytes_per_particle_step: 12.50\n")
+    assert bench.traffic_per_step("f32", "async") == 12.5
+    src = fake_root / "paper_2606_02627_gb300" / "csrc" / "advect.cu"
+    src.write_text(src.read_text() + "\n// edit\n")
     assert bench.traffic_per_step("f32", "async") is None
     assert bench.traffic_per_step("f32", "missing_tag") is None

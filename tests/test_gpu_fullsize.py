@@ -7,7 +7,9 @@
   vertices inside the domain, total steps = sum of lengths - 1).
 * 1024^3 turbulence (seed 2), 4M seeds, max 1000 steps, FP32 / FX21 / BF16 /
   FP16 storage: vertex error on the first 10k seeds against the FP64 oracle on
-  the FP32 field (max and p99 reported; bounds asserted for FP32 and FX21).
+  the FP32 field (max and p99 reported; the 1e-3 FP32 bound and the 5e-2
+  precision bound asserted on every vertex for FP32 and FX21, at the 99th
+  percentile for BF16 and FP16).
 """
 import numpy as np
 import pytest
@@ -132,3 +134,7 @@ def test_1024_precision_forms_error_on_10k_seeds(ctx):
         torch.cuda.empty_cache()
     assert report["f32"][0] <= 1e-3
     assert report["fx21"][0] <= 5e-2
+    # BF16 and FP16 meet the stated 5e-2-cell bound at the 99th percentile of
+    # the vertices (their largest errors are reported, not bounded)
+    assert report["bf16"][1] <= 5e-2
+    assert report["f16"][1] <= 5e-2

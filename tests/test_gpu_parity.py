@@ -2,9 +2,10 @@
 
 Inputs are seeded and synthetic; sizes keep the oracle to seconds while
 spanning several bricks and ragged brick edges.  Tolerances (cells):
-FP32 fields 1e-3 (the stated bound after 1000 steps); BF16/FP16 fields 5e-2
-against the oracle on the FP32 field and 2e-3 against the oracle on the
-dequantised field (which isolates the arithmetic).
+FP32 fields 1e-3 for every kernel (the stated bound after 1000 steps); the
+compact storage types 2e-3 against the oracle on their own dequantised
+samples (which isolates the arithmetic), and FX21 5e-2 against the oracle on
+the FP32 field (the stated precision bound).
 """
 import numpy as np
 import pytest
@@ -105,10 +106,16 @@ def test_single_brick_analytic_fields(ctx, kernel, which):
     ref = oracle.trace_streamlines(F, g.origin, g.spacing, seeds, dt, 500, eps=1e-6)
     fld = make_field(ctx, g, F, layout="global" if kernel == "per_seed" else "linear")
     _, lines = run(ctx, fld, seeds, dt, 500, kernel=kernel)
-    # the plain per-seed kernel keeps float32 global positions (rounding ~4e-6
-    # cells per step at 64 cells); the bricked kernels keep cell + fraction
-    st = compare_lines(lines, g, ref, tol=FP32_TOL if kernel != "per_seed" else 3e-3)
+    st = compare_lines(lines, g, ref, tol=FP32_TOL)
     assert st["vertices"] > 100_000
+    if kernel == "per_seed":
+        # the plain kernel reads the global float3 array, the persistent one
+        # its brick: the same samples and the same operations, so the same bits
+        lin = make_field(ctx, g, F, layout="linear")
+        _, pers = run(ctx, lin, seeds, dt, 500, kernel="persistent")
+        assert torch.equal(lines.offsets, pers.offsets)
+        assert torch.equal(lines.vertices, pers.vertices)
+        assert torch.equal(lines.status, pers.status)
 
 
 # ---------------------------------------------------------------- bricks invisible
@@ -228,15 +235,19 @@ def test_turbulence_fp32_bricked_1000_steps(ctx, turb64, layout):
     print("fp32", st["max_err"], st["p99"], st["ties"])
 
 
-# measured on this field after 1000 steps (max, p99 vertex error in cells vs the
-# FP32-field oracle): bf16 8.0 / 0.34, f16 0.72 / 0.055 -- the 8- and 11-bit
-# mantissas cannot meet 5e-2; the 21-bit fixed-point form, in the same 8 bytes
-# per sample, must meet it for every vertex.
-QUANT_BOUNDS = {"bf16": (None, 0.5), "f16": (None, 0.1), "fx21": (5e-2, 5e-3)}
+# The stated precision bound is 5e-2 cells against the FP64 oracle on the FP32
+# field.  FX21 (21-bit fixed point in the same 8 bytes per sample) must meet it
+# for every vertex of this field.  BF16 and FP16 are held to the arithmetic
+# bound against the oracle on their own dequantised samples; their error
+# against the FP32 field is reported here (this 1000-step, strongly stretching
+# field amplifies their 8- and 11-bit mantissas beyond 5e-2) and asserted at
+# the 99th percentile on the 1024^3 precision workload, where the stated bound
+# holds (test_gpu_fullsize).
+FX21_MAX_ERR = 5e-2
 
 
 @pytest.mark.parametrize("dtype,layout", [("bf16", "linear"), ("f16", "linear"), ("bf16", "cell8"),
-                                          ("fx21", "linear"), ("fx21", "cell8")])
+                                          ("f16", "cell8"), ("fx21", "linear"), ("fx21", "cell8")])
 def test_turbulence_quantized(ctx, turb64, dtype, layout):
     g, F, seeds, dt, ref = turb64
     fld = make_field(ctx, g, F, bricks=(4, 4, 4), dtype=dtype, layout=layout)
@@ -249,10 +260,8 @@ def test_turbulence_quantized(ctx, turb64, dtype, layout):
     # the precision form against the FP32-field oracle (common prefixes of every line)
     st = compare_lines(lines, g, ref, tol=1e9, tie_cells=0.5)
     print(dtype, layout, "vs dequantised", st_q["max_err"], "vs fp32 field max", st["max_err"], "p99", st["p99"])
-    max_bound, p99_bound = QUANT_BOUNDS[dtype]
-    assert st["p99"] <= p99_bound
-    if max_bound is not None:
-        assert st["max_err"] <= max_bound
+    if dtype == "fx21":
+        assert st["max_err"] <= FX21_MAX_ERR
 
 
 # ---------------------------------------------------------------- step() and edge cases
@@ -274,6 +283,61 @@ def test_step_calls_equal_one_trace(ctx, turb64, layout):
     lines = tr.get_lines()
     ref300 = oracle.trace_streamlines(F, g.origin, g.spacing, seeds, dt, 300, eps=1e-6)
     compare_lines(lines, g, ref300, tol=FP32_TOL)
+
+
+@pytest.mark.parametrize("layout,timed", [("linear", False), ("cell8", False), ("cell8", True)])
+def test_round_cap_stops_with_consistent_partial_lines(ctx, turb64, layout, timed):
+    # trace() stops when the rounds are all gone and nothing is left (Sec. 3.2);
+    # a round cap below that stops it early with SG_ERR_ROUND_LIMIT.  The lines
+    # written so far must read back consistently (every vertex the oracle's),
+    # and calling trace() again continues them to the uncapped result.
+    from paper_2606_02627_gb300 import _lib, api
+    g, F, seeds, dt, _ = turb64
+    ref300 = oracle.trace_streamlines(F, g.origin, g.spacing, seeds, dt, 300, eps=1e-6)
+    fld = make_field(ctx, g, F, bricks=(3, 2, 2), layout=layout)
+    spr = 13
+    tr = api.Tracer(ctx, fld, capacity=len(seeds), dt=dt, max_steps=300, steps_per_round=spr, max_rounds=1)
+    tr.upload_seeds(torch.from_numpy(seeds).cuda())
+
+    def one_call():
+        try:
+            if timed:
+                tr.trace_timed()
+            else:
+                tr.trace()
+                tr.check()
+            return True
+        except _lib.StreamGBError as e:
+            assert e.code == _lib.SG_ERR_ROUND_LIMIT, e
+            return False
+
+    assert not one_call()
+    lines = tr.get_lines()
+    torch.cuda.synchronize()
+    st = lines.status.cpu().numpy() & 0x7F
+    lens = lines.lengths().cpu().numpy()
+    assert (st == 0).sum() > len(seeds) // 2                  # most lines are still running
+    assert lens.max() <= spr + 1                               # one round: at most steps_per_round steps
+    assert (lens[st == 0] >= 1).all()
+    glines = split_lines(lines, g)
+    for i in range(len(seeds)):
+        r = ref300.line(i)
+        k = min(len(glines[i]), len(r))
+        if st[i] == 0:
+            assert len(glines[i]) <= len(r)
+        if k:
+            assert np.abs(glines[i][:k] - r[:k]).max() <= FP32_TOL, i
+    calls = 1
+    while not one_call():
+        calls += 1
+        assert calls < 300
+    final = tr.get_lines()
+    compare_lines(final, g, ref300, tol=FP32_TOL)
+    # the same bits as one uncapped trace with the same steps per round
+    _, whole = run(ctx, fld, seeds, dt, 300, steps_per_round=spr)
+    assert torch.equal(final.offsets, whole.offsets)
+    assert torch.equal(final.vertices, whole.vertices)
+    assert torch.equal(final.status, whole.status)
 
 
 def test_step_reports_active_lines(ctx):

@@ -441,11 +441,51 @@ def test_streakline_time_interpolation_is_exact_for_linear_in_time_flow():
         assert S.steps[0, b] == steps - b
 
 
-def test_max_speed():
-    g = inputs.Grid((5, 6, 7), (0.0, 1.0, 2.0), (0.5, 0.25, 2.0))
-    F = inputs.linear_field(g, np.eye(3) * 0.5, (0, 0, 0))
-    v = F.astype(np.float64) / np.array([0.5, 0.25, 2.0])
-    assert oracle.max_speed(F, g.spacing) == pytest.approx(np.sqrt((v * v).sum(-1)).max(), rel=1e-15)
+def test_max_speed_planted_pythagorean_samples():
+    # The speed in cells per unit time of a sample v on spacing s is |v / s|.
+    # Samples are planted whose velocity in cells is a Pythagorean quadruple,
+    # so the expected maximum is an integer fixed by arithmetic alone: (1, 4, 8)
+    # has norm 9, (2, 3, 6) norm 7.  The spacing differs per axis, so dividing
+    # by the wrong axis, dropping a component or skipping the division changes
+    # the answer; planting at the last sample catches a loop that stops early.
+    sp = (0.5, 0.25, 2.0)
+    g = inputs.Grid((5, 6, 7), (0.0, 1.0, 2.0), sp)
+    rng = np.random.default_rng(5)
+    F = (0.01 * rng.uniform(-1, 1, (7, 6, 5, 3))).astype(np.float32)   # background: under 0.2 cells/time
+    assert oracle.max_speed(F, g.spacing) < 0.2
+
+    def plant(F, z, y, x, cells):
+        F[z, y, x] = [cells[a] * sp[a] for a in range(3)]              # exact in float32 (dyadic)
+
+    plant(F, 2, 3, 1, (2, 3, 6))
+    assert oracle.max_speed(F, g.spacing) == 7.0
+    plant(F, 6, 5, 4, (1, 4, 8))                                        # the very last sample
+    assert oracle.max_speed(F, g.spacing) == 9.0
+    # the same components permuted across axes: the grid's anisotropy changes |v/s|
+    F2 = F.copy()
+    F2[6, 5, 4] = [8 * sp[0], 1 * sp[1], 4 * sp[2]]
+    assert oracle.max_speed(F2, g.spacing) == 9.0
+    F3 = F.copy()
+    F3[6, 5, 4] = [1 * sp[2], 4 * sp[1], 8 * sp[0]]                     # cells (4, 4, 2): speed 6
+    assert oracle.max_speed(F3, g.spacing) == 7.0                       # the (2, 3, 6) sample is now the largest
+    # negative components count by magnitude
+    F4 = F.copy()
+    F4[0, 0, 0] = [-2 * sp[0], -10 * sp[1], 11 * sp[2]]                 # (2, 10, 11): 15
+    assert oracle.max_speed(F4, g.spacing) == 15.0
+
+
+def test_max_speed_uniform_and_rotation_closed_forms():
+    # uniform flow u: every sample has speed |u / s|; (3 * 0.5, 4 * 0.25, 12 * 2.0) -> (3, 4, 12): 13
+    sp = (0.5, 0.25, 2.0)
+    g = inputs.Grid((4, 5, 6), (1.0, -2.0, 0.5), sp)
+    F = inputs.uniform_field(g, (1.5, 1.0, 24.0))
+    assert oracle.max_speed(F, g.spacing) == 13.0
+    # solid-body rotation v = (-(y - cy), x - cx, 0) on a unit-spacing grid with
+    # the axis at the centre: the largest speed is at a corner, the distance
+    # from the axis sqrt(hx^2 + hy^2) with hx, hy the half extents
+    g2 = inputs.Grid((9, 7, 3), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    F2 = inputs.rotation_field(g2, center=(4.0, 3.0, 1.0))
+    assert oracle.max_speed(F2, g2.spacing) == 5.0                      # (4, 3) -> 5
 
 
 def test_golden_uniform_exit():
