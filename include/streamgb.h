@@ -68,13 +68,17 @@ enum {
  * case. */
 enum { SG_F32 = 0, SG_BF16 = 1, SG_F16 = 2, SG_FX21 = 3 };
 
-/* Sample layout inside a brick.  A sample is x, y, z and one pad: 16 B in
- * FP32, 8 B in BF16/FP16.  LINEAR is x-fastest; TILED4 groups 4x4x4 samples
+/* Sample layout inside a brick.  A LINEAR or TILED4 sample is x, y, z and one
+ * pad: 16 B in FP32, 8 B in BF16/FP16 (FX21: three 21-bit components and a
+ * flag in 8 B).  LINEAR is x-fastest; TILED4 groups 4x4x4 samples
  * contiguously (tile-major, x-fastest inside a tile).  CELL8 stores, for every
  * cell of the brick (ghost cells included, (n+2)^3 of them), the eight corner
- * samples of that cell contiguously (x fastest, then y, then z): 8x the
- * samples, so that one interpolation reads one 64 B (BF16/FP16) or 128 B
- * (FP32) record instead of eight scattered samples. */
+ * samples of that cell contiguously, so that one interpolation reads one
+ * record instead of eight scattered samples: a 96-B FP32 record holds the 24
+ * components without padding (x, then y, then z; each as the four corners of
+ * the cell's x = 0 face, then the four of its x = 1 face, in (y, z) order
+ * (0,0), (0,1), (1,0), (1,1)); a 64-B record of an 8-byte format holds the
+ * eight samples in corner order (x fastest, then y, then z). */
 enum { SG_LAYOUT_LINEAR = 0, SG_LAYOUT_TILED4 = 1, SG_LAYOUT_CELL8 = 2 };
 
 /* Line status (uint8 per line).  Bit 7 (SG_LINE_TIE) marks a boundary tie: a
@@ -193,21 +197,33 @@ sg_status sg_field_brick_cells(const sg_field *f, int64_t n_out[3]);
 
 /* Sets slot `slot` from a global FP32 AoS array [dims2][dims1][dims0][3]
  * (device or page-locked host memory): cuts the bricks, fills the ghost
- * shells and encodes BF16/FP16 with per-brick scales.  Asynchronous. */
+ * shells and encodes BF16/FP16 with per-brick scales.  The paper's setField
+ * with a structured field of float3 voxels (Sec. 3.2, Sec. 3.3), here cut
+ * into the macrocells with their halos (Sec. 3.1.1) by the library.
+ * Errors: SG_ERR_INVALID_ARG for a NULL pointer or a slot out of range,
+ * SG_ERR_CUDA for a failed launch or copy.  Asynchronous. */
 sg_status sg_field_set_global(sg_field *f, int32_t slot, const float *vec3, void *stream);
 
 /* Sets one brick of slot `slot` from its own (n+3)^3 FP32 AoS samples,
  * ghost shell included, as the application holds it (device or page-locked
  * host memory); samples are those at global indices b*n-1 .. b*n+n+1 per
- * axis, which the caller clamps (or fills) at the domain faces itself.
- * Asynchronous. */
+ * axis, which the caller clamps (or fills) at the domain faces itself.  This
+ * is the paper's per-rank field creation: each macrocell's data with its
+ * user-defined halo, assembled by the application from its own
+ * decomposition (Sec. 3.1.1, Sec. 3.2).  Errors: SG_ERR_INVALID_ARG for a
+ * brick or slot out of range or a NULL pointer, SG_ERR_CUDA for a failed
+ * launch or copy.  Asynchronous. */
 sg_status sg_field_set_brick(sg_field *f, int32_t slot, int32_t bx, int32_t by, int32_t bz,
                              const float *vec3_with_halo, void *stream);
 
 /* Streams time slice `slice` from page-locked host memory (global FP32 AoS)
  * into slot slice % n_slots on `stream`, and records that the slot holds the
  * slice once the stream reaches the end of the copy.  A tracer step that
- * needs the slice waits for it on its own stream (cudaStreamWaitEvent). */
+ * needs the slice waits for it on its own stream (cudaStreamWaitEvent).  The
+ * paper's unsteady input: one field per time step, set with setField(f,
+ * timeStep) and selected by the simulation time in step() (Sec. 3.2, Listing
+ * 2).  Errors: SG_ERR_INVALID_ARG for pageable or NULL memory or a negative
+ * slice, SG_ERR_CUDA for a failed copy.  Asynchronous. */
 sg_status sg_field_stream_slice(sg_field *f, int32_t slice, const float *pinned_host, void *stream);
 
 /* Largest |v / spacing| over the stored (decoded) samples of `slot`, in cells
@@ -463,7 +479,7 @@ sg_status sg_umesh_sample(sg_umesh *m, const float *points, int64_t n, float *ve
 /* Streamlines from n seeds (device, world): line i's vertices go to slab +
  * 3 i (max_steps + 1) (device), its vertex count to length[i], its status
  * (SG_LINE_*, tie bit for EXIT margins < 1e-3) and margin likewise (all
- * device).  Compact with sg_lines_compact_static.  Asynchronous. */
+ * device).  Compact with sg_lines_compact.  Asynchronous. */
 sg_status sg_umesh_trace(sg_umesh *m, const float *seeds, int64_t n, double dt, int32_t max_steps, float eps,
                          float *slab, uint32_t *length, uint8_t *status, float *margin, void *stream);
 
@@ -562,14 +578,32 @@ sg_status sg_batch_get_lines(sg_batch *b, int64_t request_id, int64_t *n_lines, 
  * (its readback) is done.  Its id becomes invalid. */
 sg_status sg_batch_release(sg_batch *b, int64_t request_id, void *stream);
 
+/* ------------------------------------------------------- line compaction */
+
+/* Bytes of scan scratch sg_lines_compact needs for n_lines lines: one 8-byte
+ * sum per 4096 lines plus 64 bytes. */
+sg_status sg_lines_compact_scratch_bytes(int64_t n_lines, size_t *bytes);
+
+/* Compacts per-line vertex slabs into CSR: getLines / assembleOutput (Fig. 4,
+ * Listing 2) for slabs a caller holds itself (the unstructured field's trace,
+ * a partitioned trace's merged lines).  Same arguments as
+ * sg_lines_compact_static below, plus a caller-owned device scratch buffer
+ * (8-byte aligned, at least sg_lines_compact_scratch_bytes(n_lines) bytes)
+ * that the call uses on `stream` and that may be reused once the stream has
+ * passed it.  Calls with separate scratch buffers may run concurrently.
+ * Errors: SG_ERR_INVALID_ARG for a NULL or short buffer or sizes out of
+ * range.  Asynchronous on `stream`. */
+sg_status sg_lines_compact(const float *slab, int64_t max_vertices_per_line, const uint32_t *lengths,
+                           int64_t n_lines, void *scratch, size_t scratch_bytes, int64_t *offsets, float *vertices,
+                           void *stream);
+
 /* ------------------------------------------------ allocation-free compaction */
 
 /* The paper has no counterpart to this call: it is a service for callers that
- * must not allocate device memory, such as code running while a stream is
- * captured in global mode (cudaMalloc is refused then), a simulation that has
- * handed all of HBM to its own pool and lends its buffers to the field-line
- * pass in situ, or a loop that cannot take the device-wide synchronisation
- * that cudaMalloc/cudaFree may cause.
+ * must not allocate device memory, such as a simulation that has handed all
+ * of HBM to its own pool and lends its buffers to the field-line pass in
+ * situ, or a loop that cannot take the device-wide synchronisation that
+ * cudaMalloc/cudaFree may cause.
  *
  * Compacts per-line vertex slabs into CSR, as sg_tracer_get_lines does, but
  * its scan scratch lives in a fixed array inside the library's device memory
@@ -586,7 +620,10 @@ sg_status sg_batch_release(sg_batch *b, int64_t request_id, void *stream);
  * n_lines above 16,777,216 (4096 chunks of 4096 lines), or
  * max_vertices_per_line of 2^28 or more, is rejected with SG_ERR_INVALID_ARG.  The first call on a device looks up the scratch
  * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  All calls on a device share the
+ * that first call before any stream capture.  The address stays cached for the
+ * life of the process: after a cudaDeviceReset of that device (which frees
+ * the library's copy of the array with the context) the call must not be used
+ * on it again in the same process.  All calls on a device share the
  * one scratch array and it keeps the last call's contents: calls that overlap
  * on the GPU (different streams, or graphs launched concurrently) race and
  * must be ordered by the caller.  Asynchronous on `stream`. */

@@ -115,6 +115,8 @@ SIGNATURES = {
     "sg_seeds_plane": ([P, P, P, i64, i64, P, P], i32),
     "sg_seeds_box": ([P, P, i64, ctypes.c_uint64, ctypes.c_uint64, P, P], i32),
     "sg_lines_compact_static": ([P, i64, P, i64, P, P, P], i32),
+    "sg_lines_compact_scratch_bytes": ([i64, ctypes.POINTER(sz)], i32),
+    "sg_lines_compact": ([P, i64, P, i64, P, sz, P, P, P], i32),
     "sg_batch_required_bytes": ([P, ctypes.POINTER(sg_batch_desc), ctypes.POINTER(sz)], i32),
     "sg_batch_create": ([P, ctypes.POINTER(sg_batch_desc), P, sz, PP], i32),
     "sg_batch_destroy": ([P], i32),

@@ -433,23 +433,32 @@ class UMesh:
         return v[:n], c[:n]
 
     def trace(self, seeds, dt: float, max_steps: int, eps: float = 1e-6, stream=None) -> Lines:
-        """Streamlines from world seeds, compacted to CSR (device)."""
+        """Streamlines from world seeds, compacted to CSR (device).  Every
+        buffer is allocated, and every call enqueued, on `stream` (the current
+        stream if None), which the call synchronises once to size the CSR."""
         dev = f"cuda:{self.ctx.device}"
-        s = torch.as_tensor(seeds, dtype=torch.float32).to(dev).contiguous()
-        n = s.shape[0]
-        W = int(max_steps) + 1
-        slab = torch.empty((max(n, 1), W, 3), dtype=torch.float32, device=dev)
-        length = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
-        st = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
-        mg = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
-        call("sg_umesh_trace", self.h, _ptr(s), n, float(dt), int(max_steps), float(eps), _ptr(slab), _ptr(length),
-             _ptr(st), _ptr(mg), _stream(stream))
-        off = torch.empty(n + 1, dtype=torch.int64, device=dev)
-        call("sg_lines_compact_static", _ptr(slab), W, _ptr(length), n, _ptr(off), None, _stream(stream))
-        total = int(off[n].item()) if n else 0
-        vert = torch.empty((max(total, 1), 3), dtype=torch.float32, device=dev)
-        call("sg_lines_compact_static", _ptr(slab), W, _ptr(length), n, _ptr(off), _ptr(vert), _stream(stream))
-        src = torch.arange(n, dtype=torch.int32, device=dev)
+        strm = torch.cuda.current_stream(dev) if stream is None else stream
+        with torch.cuda.stream(strm):
+            s = torch.as_tensor(seeds, dtype=torch.float32).to(dev).contiguous()
+            n = s.shape[0]
+            W = int(max_steps) + 1
+            slab = torch.empty((max(n, 1), W, 3), dtype=torch.float32, device=dev)
+            length = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+            st = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+            mg = torch.empty(max(n, 1), dtype=torch.float32, device=dev)
+            call("sg_umesh_trace", self.h, _ptr(s), n, float(dt), int(max_steps), float(eps), _ptr(slab),
+                 _ptr(length), _ptr(st), _ptr(mg), _stream(strm))
+            nsc = ctypes.c_size_t()
+            call("sg_lines_compact_scratch_bytes", n, ctypes.byref(nsc))
+            scratch = torch.empty(max(nsc.value, 8), dtype=torch.uint8, device=dev)
+            off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+            call("sg_lines_compact", _ptr(slab), W, _ptr(length), n, _ptr(scratch), nsc.value, _ptr(off), None,
+                 _stream(strm))
+            total = int(off[n].item()) if n else 0
+            vert = torch.empty((max(total, 1), 3), dtype=torch.float32, device=dev)
+            call("sg_lines_compact", _ptr(slab), W, _ptr(length), n, _ptr(scratch), nsc.value, _ptr(off),
+                 _ptr(vert), _stream(strm))
+            src = torch.arange(n, dtype=torch.int32, device=dev)
         return Lines(off, vert[:total], st[:n], mg[:n], src)
 
     def close(self):

@@ -144,56 +144,89 @@ constexpr unsigned COPY_WAIT_PASSES = 1u << 24;
 // every one of the four samples of a step is a load that the whole warp
 // waits for, so the warp runs at the pace of its slowest lane: at nearly
 // every sample some lane has just entered a cell whose record is not in L1.
+//
 // Here each lane keeps the record of the cell of its current sample point in
-// its own shared-memory slot and runs one RK4 stage per pass of the warp's
-// loop.  When a stage point falls in another cell, the lane starts one bulk
-// copy of that record by the TMA engine (cp.async.bulk) into its slot,
-// completing on its own mbarrier, and sits out the passes until the copy has
-// landed while the other lanes go on.  A slot is the record plus 16 bytes of
+// its own shared-memory slot.  A pass of the warp's loop runs the four RK4
+// stages in order, unrolled: iteration s runs stage s for every lane that is
+// at stage s and holds the record its sample point needs, so a lane that
+// starts the pass at stage 0 completes a whole step, and the end of the step
+// (new P0, vertex, brick test) runs for those lanes together.  When a stage
+// point falls in another cell (about one sample in seventeen at h = 0.5
+// cell), the lane starts one bulk copy of that record by the TMA engine
+// (cp.async.bulk) into its slot, completing on its own mbarrier, and sits out
+// the rest of the pass; the next pass it resumes at that stage.  The per-pass
+// bookkeeping (refill vote, copy completion, hand-off appends) is shared by
+// the up to four stages of a pass.  A slot is the record plus 16 bytes of
 // padding (112 bytes for FP32, 80 for the 8-byte formats): with that stride
 // the 16-byte reads of eight consecutive lanes fall in eight different bank
-// groups.  The stage arithmetic is
-// rk4_bricked's, operation for operation, so both kernels produce the same
-// bits.
+// groups.  The stage arithmetic is rk4_bricked's, operation for operation, so
+// both kernels produce the same bits.
+//
+// Vertices leave in 48-byte runs: every lane of a warp ends its step in the
+// same iteration, and three scattered 4-byte stores per lane at that point
+// (one per component, 32 lines at once) stall the load/store pipe that the
+// next stage's slot reads go through.  Instead each lane stages its line's
+// vertices in shared memory (16 bytes per vertex, four of them) and writes
+// the four vertices of a slab row position 4j .. 4j+3 as three 16-byte
+// stores once the last of them is done (slab rows are a multiple of four
+// vertices long, so such a run starts at a 16-byte boundary).  Vertices of a
+// run that another lane (or the upload) wrote, and the vertices of an
+// unfinished run when the particle leaves the lane, go out as 4-byte stores.
 template <int DT>
-__global__ void __launch_bounds__(256, DT == SG_F32 ? 4 : (DT == SG_F16 ? 0 : 3)) round_async_kernel(const __grid_constant__ LineParams P)
+__global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_constant__ LineParams P)
 {
     constexpr int NCH = Record<DT>::chunks;
     constexpr unsigned SLOT = (NCH + 1) * 16;              // bytes per lane slot
-    extern __shared__ uint4 slots[];                       // [blockDim][SLOT bytes], then blockDim barriers
+    // vertex staging per lane: four 16-byte vertices, then the line's slab
+    // row pointer and the first vertex this lane writes for its particle
+    // (read only when vertices leave, so they need no registers)
+    constexpr unsigned VBUF = 80;
+    // [blockDim][SLOT bytes] record slots, [blockDim][VBUF bytes] vertex
+    // staging, then blockDim barriers
+    extern __shared__ uint4 slots[];
     const unsigned tid = threadIdx.x, nthr = blockDim.x;
     const unsigned lane = tid & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const uint4 *my_slot = slots + tid * (SLOT / 16);
-    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + nthr * (SLOT / 16)) + tid);
+    uint4 *my_slot = slots + tid * (SLOT / 16);
+    uint4 *vbuf = slots + nthr * (SLOT / 16) + tid * (VBUF / 16);
+    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + nthr * ((SLOT + VBUF) / 16)) + tid);
     const uint32_t slot = smem_addr(my_slot);
     mbar_init(bar, 1);
     mbar_init_fence();
     __syncwarp();
 
     const DevField &F = P.F;
-    const uint32_t q_count = P.ctrl->q_count;
-    const uint32_t horizon = P.ctrl->horizon;
+    // the round's queue length and step horizon: constant while the kernel
+    // runs, read where they are needed (refills, particle events) rather than
+    // held in registers across the loop
+    const uint32_t *q_count_p = &P.ctrl->q_count;
+    const uint32_t *horizon_p = &P.ctrl->horizon;
     bool active = false, pending = false;
     bool inflight = false;                                 // a copy may still land in the slot
-    bool drained = q_count == 0;
-    // four passes per step
-    uint32_t drain_left = P.drain_steps >= 0x20000000u ? 0xffffffffu : P.drain_steps * 4u;
+    bool drained = __ldg(q_count_p) == 0;
+    // one pass per step once a lane's records are at hand
+    uint32_t drain_left = P.drain_steps;
     unsigned parity = 0, waited = 0;
     int c[3] = {0, 0, 0}, q[3] = {0, 0, 0};               // P0 and the current sample point
     float f[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};
-    // k1-k3 and ds: x and y as packed pairs, z alone
-    f32x2 k1xy = 0, k2xy = 0, k3xy = 0, dsxy = 0;
-    float k1z = 0.f, k2z = 0.f, k3z = 0.f, dsz = 0.f;
+    // k1 and k2 (k2 + k3 after stage 2), the step factor: x and y as packed
+    // pairs, z alone
+    f32x2 k1xy = 0, k23xy = 0, dsxy = 0;
+    float k1z = 0.f, k23z = 0.f, dsz = 0.f;
     uint32_t line = 0, step = 0, stage = 0;
     // steps the lane may take before its step horizon or the round's step
     // budget stops it: min(horizon - step, steps_per_round - steps this round)
     int left = 0;
-    uint32_t held = 0xffffffffu, wanted = 0;              // cell of the record in the slot / in flight
+    uint32_t held = 0xffffffffu;                           // cell of the record in (or on its way to) the slot
     BrickRef<DT> br;
     br.data = nullptr;
     br.scale = 1.0f;
     for (int a = 0; a < 3; ++a) br.lo[a] = br.hi[a] = 0;
+    // the record index of cell q in the brick is q.z C1 C0 + q.y C0 + q.x + cbase;
+    // the brick's first owned cell and its extent (lo, span per axis) sit in
+    // the 16-byte pad after the lane's record slot (the bulk copy writes only
+    // the record) and in the vertex staging area: the per-step brick test
+    // reads them there
+    int cbase = 0;
     // cells [box_lo, box_lo + box_span] per axis lie inside the domain's
     // cells (not on its last sample layer) and inside the brick's ghost
     // shell: a stage point there needs neither the EXIT nor the HALO test
@@ -201,19 +234,14 @@ __global__ void __launch_bounds__(256, DT == SG_F32 ? 4 : (DT == SG_F16 ? 0 : 3)
     unsigned box_span[3] = {0u, 0u, 0u};
     // |v|^2 at or above e2min (before the brick scale) means |v| >= eps
     float e2min = 0.f;
-    float *vp = nullptr;                                   // where the line's next vertex goes
 
     // the cell of sample point q within the brick's records
-    auto cell_of = [&]() {
-        const int sx = q[0] - br.lo[0] + 1, sy = q[1] - br.lo[1] + 1, sz = q[2] - br.lo[2] + 1;
-        return (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
-    };
+    auto cell_of = [&]() { return (uint32_t)((q[2] * F.C[1] + q[1]) * F.C[0] + q[0] + cbase); };
     // copy the record of `cell` into the slot
     auto fetch = [&](uint32_t cell) {
         bulk_copy_arrive(slot, br.data + (long long)cell * record_elems<DT>(), NCH * 16u, bar);
         inflight = true;
-        held = 0xffffffffu;
-        wanted = cell;
+        held = cell;
         pending = true;
         waited = 0;
     };
@@ -226,10 +254,12 @@ __global__ void __launch_bounds__(256, DT == SG_F32 ? 4 : (DT == SG_F16 ? 0 : 3)
             uint32_t base = 0;
             if ((int)lane == leader) base = atomicAdd(&P.ctrl->q_head, (uint32_t)__popc(need));
             base = __shfl_sync(SG_FULL_MASK, base, leader);
+            const uint32_t q_count = __ldg(q_count_p);
             if (base + (uint32_t)__popc(need) >= q_count) drained = true;
             if (!active) {
-                const uint32_t my = base + __popc(need & lt);
+                const uint32_t my = base + __popc(need & ((1u << lane) - 1u));
                 if (my < q_count) {
+                    const uint32_t horizon = __ldg(horizon_p);
                     load_particle(P.q + my, c, f, line, step);
                     brick_of<DT>(F, c, br);
                     float dtc[3];
@@ -255,7 +285,16 @@ __global__ void __launch_bounds__(256, DT == SG_F32 ? 4 : (DT == SG_F16 ? 0 : 3)
                         const float e = (DT == SG_F32) ? P.eps : __fdiv_ru(P.eps, br.scale);
                         e2min = __fmul_ru(e, e);
                     }
-                    vp = P.slab + ((long long)line * P.W + step + 1) * 3;
+                    {
+                        const unsigned long long row =
+                            reinterpret_cast<unsigned long long>(P.slab + (long long)line * P.W * 3);
+                        const uint32_t sp0 = (uint32_t)(br.hi[0] - br.lo[0]), sp1 = (uint32_t)(br.hi[1] - br.lo[1]);
+                        vbuf[4] = make_uint4((uint32_t)row, (uint32_t)(row >> 32), step + 1,
+                                             (uint32_t)(br.hi[2] - br.lo[2]));
+                        my_slot[NCH] = make_uint4((uint32_t)br.lo[0], (uint32_t)br.lo[1], (uint32_t)br.lo[2],
+                                                  sp0 | (sp1 << 16));
+                        cbase = -(((br.lo[2] - 1) * F.C[1] + (br.lo[1] - 1)) * F.C[0] + (br.lo[0] - 1));
+                    }
                     left = step >= horizon ? 0 : (int)min(horizon - step, P.steps_per_round);
                     active = true;
                     stage = 0;
@@ -270,7 +309,6 @@ __global__ void __launch_bounds__(256, DT == SG_F32 ? 4 : (DT == SG_F16 ? 0 : 3)
         bool gave_up = false;
         if (pending) {
             if (mbar_done(bar, parity)) {
-                held = wanted;
                 parity ^= 1u;
                 pending = false;
                 inflight = false;
@@ -287,9 +325,10 @@ __global__ void __launch_bounds__(256, DT == SG_F32 ? 4 : (DT == SG_F16 ? 0 : 3)
 
         int ev = EV_NONE, st = SG_LINE_ACTIVE;
         float margin = INFINITY;
-        bool run = active && !pending;
-        if (run && stage == 0 && left <= 0) {
-            if (step >= horizon) {
+        bool go = active && !pending;
+        bool run_done = false;                       // this pass completed vertex 4j+3 of the row
+        if (go && stage == 0 && left <= 0) {
+            if (step >= __ldg(horizon_p)) {
                 if (step >= P.max_steps) {
                     ev = EV_STOP;
                     st = SG_LINE_MAXSTEPS;
@@ -299,95 +338,170 @@ __global__ void __launch_bounds__(256, DT == SG_F32 ? 4 : (DT == SG_F16 ? 0 : 3)
             } else {
                 ev = EV_APPEND;                   // the round's step budget is spent
             }
-            run = false;
+            go = false;
         }
-        if (run) {
-            // one stage, the same instructions at every stage (the lanes of a
-            // warp are at different stages): sample, k = v dt/h, and the next
-            // point P0 + w k (stages 0-2) or P' (stage 3)
-            Record<DT> R;
+        // the four stages; iteration S runs stage S: sample, k = v dt/h, and
+        // the next point P0 + k1/2, P0 + k2/2, P0 + k3 or P'
+#pragma unroll 1
+        for (int S = 0; S < 4; ++S) {
+            if (go && stage == (uint32_t)S) {
+                Record<DT> R;
 #pragma unroll
-            for (int k = 0; k < NCH; ++k) R.r[k] = my_slot[k];
-            bool bad_flag;                           // FX21: a corner's stored flag
-            const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad_flag);
-            const f32x2 vxy = pk2(v.x, v.y);
-            const float2 sq = upk2(mul2(vxy, vxy));
-            const float s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
-            const f32x2 kxy = mul2(vxy, dsxy);
-            const float kz = __fmul_rn(v.z, dsz);
-            const bool last = stage == 3;
-            const float w = stage < 2 ? 0.5f : 1.0f;   // P1, P2 = P0 + k/2; P3 = P0 + k3
-            const float2 fin = upk2(mul2(add2(add2(k1xy, kxy), mul2(pk2(2.0f, 2.0f), add2(k2xy, k3xy))),
-                                         pk2(1.0f / 6.0f, 1.0f / 6.0f)));
-            const float finz = __fmul_rn(__fadd_rn(__fadd_rn(k1z, kz), __fmul_rn(2.0f, __fadd_rn(k2z, k3z))), 1.0f / 6.0f);
-            const float2 wk = upk2(mul2(pk2(w, w), kxy));
-            locate(f[0], last ? fin.x : wk.x, c[0], q[0], g[0]);
-            locate(f[1], last ? fin.y : wk.y, c[1], q[1], g[1]);
-            locate(f[2], last ? finz : w * kz, c[2], q[2], g[2]);
-            k1xy = stage == 0 ? kxy : k1xy;
-            k2xy = stage == 1 ? kxy : k2xy;
-            k3xy = stage == 2 ? kxy : k3xy;
-            k1z = stage == 0 ? kz : k1z;
-            k2z = stage == 1 ? kz : k2z;
-            k3z = stage == 2 ? kz : k3z;
-            const bool in_box = (unsigned)(q[0] - box_lo[0]) <= box_span[0] &&
-                                (unsigned)(q[1] - box_lo[1]) <= box_span[1] &&
-                                (unsigned)(q[2] - box_lo[2]) <= box_span[2];
-            // a non-finite component makes |v|^2 non-finite (the float formats)
-            const bool maybe_bad = (DT == SG_FX21) ? bad_flag : !(s2 < INFINITY);
-            if (maybe_bad || (stage == 0 && !(s2 >= e2min)) || !in_box) {
-                // the tests in full (rare): a sample that may not be finite, a
-                // speed that may be below eps, a point near the domain or
-                // brick boundary
-                const bool bad = (DT == SG_FX21) ? bad_flag : bad3(v);
-                float sp = sqrtf(s2);
-                if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
-                if (bad) {
-                    st = SG_LINE_NANFIELD;
-                } else if (stage == 0 && sp < P.eps) {
-                    margin = (P.eps - sp) / P.eps;
-                    st = SG_LINE_STAGNANT;
-                } else if (!in_domain(F, q, g)) {
-                    margin = out_dist(F, q, g);
-                    st = SG_LINE_EXIT;
-                } else if (!last && ((unsigned)(q[0] - br.lo[0] + 1) > (unsigned)(F.S[0] - 2) ||
-                                     (unsigned)(q[1] - br.lo[1] + 1) > (unsigned)(F.S[1] - 2) ||
-                                     (unsigned)(q[2] - br.lo[2] + 1) > (unsigned)(F.S[2] - 2))) {
-                    st = SG_LINE_HALO;
+                for (int k = 0; k < NCH; ++k) R.r[k] = my_slot[k];
+                bool bad_flag;                       // FX21: a corner's stored flag
+                const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad_flag);
+                const f32x2 vxy = pk2(v.x, v.y);
+                const f32x2 kxy = mul2(vxy, dsxy);
+                const float kz = __fmul_rn(v.z, dsz);
+                float dxy_x, dxy_y, dz;              // offset of the next point from P0
+                if (S == 0) {
+                    k1xy = kxy;
+                    k1z = kz;
+                } else if (S == 1) {
+                    k23xy = kxy;
+                    k23z = kz;
+                } else if (S == 2) {
+                    k23xy = add2(k23xy, kxy);
+                    k23z = __fadd_rn(k23z, kz);
                 }
-            }
-            bool go = st == SG_LINE_ACTIVE;
-            if (!go) ev = EV_STOP;
-            if (go && last) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    c[a] = q[a];
-                    f[a] = g[a];
+                if (S < 3) {
+                    const float w = S < 2 ? 0.5f : 1.0f;   // P1, P2 = P0 + k/2; P3 = P0 + k3
+                    const float2 wk = upk2(mul2(pk2(w, w), kxy));
+                    dxy_x = wk.x;
+                    dxy_y = wk.y;
+                    dz = w * kz;
+                } else {
+                    const float2 fin = upk2(mul2(add2(add2(k1xy, kxy), mul2(pk2(2.0f, 2.0f), k23xy)),
+                                                 pk2(1.0f / 6.0f, 1.0f / 6.0f)));
+                    dxy_x = fin.x;
+                    dxy_y = fin.y;
+                    dz = __fmul_rn(__fadd_rn(__fadd_rn(k1z, kz), __fmul_rn(2.0f, k23z)), 1.0f / 6.0f);
                 }
-                ++step;
-                --left;
-                st_na(vp, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
-                st_na(vp + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
-                st_na(vp + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
-                vp += 3;
-                const bool out = (unsigned)(c[0] - br.lo[0]) >= (unsigned)(br.hi[0] - br.lo[0]) ||
-                                 (unsigned)(c[1] - br.lo[1]) >= (unsigned)(br.hi[1] - br.lo[1]) ||
-                                 (unsigned)(c[2] - br.lo[2]) >= (unsigned)(br.hi[2] - br.lo[2]);
-                if (left <= 0 || out) {
+                locate(f[0], dxy_x, c[0], q[0], g[0]);
+                locate(f[1], dxy_y, c[1], q[1], g[1]);
+                locate(f[2], dz, c[2], q[2], g[2]);
+                const bool in_box = (unsigned)(q[0] - box_lo[0]) <= box_span[0] &&
+                                    (unsigned)(q[1] - box_lo[1]) <= box_span[1] &&
+                                    (unsigned)(q[2] - box_lo[2]) <= box_span[2];
+                // |v|^2 of the stage-0 sample, and of any sample whose values may
+                // not be finite: a non-finite component makes it non-finite
+                float s2 = 0.f;
+                bool maybe_bad;
+                if constexpr (DT == SG_FX21) {
+                    maybe_bad = bad_flag;
+                    if (S == 0) {
+                        const float2 sq = upk2(mul2(vxy, vxy));
+                        s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
+                    }
+                } else {
+                    const float2 sq = upk2(mul2(vxy, vxy));
+                    s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
+                    maybe_bad = !(s2 < INFINITY);
+                }
+                const float e2 = (DT == SG_F32) ? __fmul_ru(P.eps, P.eps) : e2min;
+                if (maybe_bad || (S == 0 && !(s2 >= e2)) || !in_box) {
+                    // the tests in full (rare): a sample that may not be finite, a
+                    // speed that may be below eps, a point near the domain or
+                    // brick boundary
+                    const bool bad = (DT == SG_FX21) ? bad_flag : bad3(v);
+                    float sp = sqrtf(s2);
+                    if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
+                    if (bad) {
+                        st = SG_LINE_NANFIELD;
+                    } else if (S == 0 && sp < P.eps) {
+                        margin = (P.eps - sp) / P.eps;
+                        st = SG_LINE_STAGNANT;
+                    } else if (!in_domain(F, q, g)) {
+                        margin = out_dist(F, q, g);
+                        st = SG_LINE_EXIT;
+                    } else if (S < 3) {
+                        const uint4 bl = my_slot[NCH];
+                        if ((unsigned)(q[0] - (int)bl.x + 1) > (unsigned)(F.S[0] - 2) ||
+                            (unsigned)(q[1] - (int)bl.y + 1) > (unsigned)(F.S[1] - 2) ||
+                            (unsigned)(q[2] - (int)bl.z + 1) > (unsigned)(F.S[2] - 2))
+                            st = SG_LINE_HALO;
+                    }
+                }
+                if (st != SG_LINE_ACTIVE) {
+                    ev = EV_STOP;
                     go = false;
-                    if (step >= horizon) {
-                        ev = step >= P.max_steps ? EV_STOP : EV_PARK;
-                        st = step >= P.max_steps ? SG_LINE_MAXSTEPS : st;
-                    } else if (out) {
-                        ev = EV_APPEND;           // destinationID(new position) != this brick
-                    }                             // else re-queued at the next pass, no fetch
+                } else if (S == 3) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        c[a] = q[a];
+                        f[a] = g[a];
+                    }
+                    ++step;
+                    --left;
+                    vbuf[step & 3u] = make_uint4(__float_as_uint(fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0])),
+                                                 __float_as_uint(fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1])),
+                                                 __float_as_uint(fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2])),
+                                                 0u);
+                    run_done = (step & 3u) == 3u;
+                    stage = 0;
+                    const uint4 bl = my_slot[NCH];
+                    const bool out = (unsigned)(c[0] - (int)bl.x) >= (bl.w & 0xffffu) ||
+                                     (unsigned)(c[1] - (int)bl.y) >= (bl.w >> 16) ||
+                                     (unsigned)(c[2] - (int)bl.z) >= vbuf[4].w;
+                    if (left <= 0 || out) {
+                        go = false;
+                        if (step >= __ldg(horizon_p)) {
+                            ev = step >= P.max_steps ? EV_STOP : EV_PARK;
+                            st = step >= P.max_steps ? SG_LINE_MAXSTEPS : st;
+                        } else {
+                            // destinationID(new position) != this brick, or the
+                            // round's step budget is spent
+                            ev = EV_APPEND;
+                        }
+                    }
+                } else {
+                    stage = S + 1;
+                }
+                if (go) {
+                    // the record of the next sample point q
+                    const uint32_t next = cell_of();
+                    if (next != held) {
+                        fetch(next);
+                        go = false;
+                    }
                 }
             }
-            stage = last ? 0 : stage + 1;
-            const uint32_t next = cell_of();
-            if (go && next != held) fetch(next);  // the record of the next sample point q
+        }
+        if (run_done) {
+            const uint4 rw = vbuf[4];
+            float *vrow = reinterpret_cast<float *>(((unsigned long long)rw.y << 32) | rw.x);
+            if (step - 3u >= rw.z) {
+                // the row's run 4j .. 4j+3 is this lane's: 48 bytes at a 16-byte boundary
+                uint4 *o = reinterpret_cast<uint4 *>(vrow + 3ll * (step - 3u));
+                const uint4 a = vbuf[0], b = vbuf[1];
+                st_na4(o, make_uint4(a.x, a.y, a.z, b.x));
+                const uint4 cc = vbuf[2];
+                st_na4(o + 1, make_uint4(b.y, b.z, cc.x, cc.y));
+                const uint4 d = vbuf[3];
+                st_na4(o + 2, make_uint4(cc.z, d.x, d.y, d.z));
+            } else {
+                for (uint32_t u = rw.z; u <= step; ++u) {
+                    const uint4 a = vbuf[u & 3u];
+                    float *o = vrow + 3ll * u;
+                    st_na(o, __uint_as_float(a.x));
+                    st_na(o + 1, __uint_as_float(a.y));
+                    st_na(o + 2, __uint_as_float(a.z));
+                }
+            }
         }
         if (__any_sync(SG_FULL_MASK, ev != EV_NONE)) {
+            if (ev != EV_NONE && (step & 3u) != 3u) {
+                // the particle leaves: the staged vertices of its unfinished run
+                const uint4 rw = vbuf[4];
+                float *vrow = reinterpret_cast<float *>(((unsigned long long)rw.y << 32) | rw.x);
+                for (uint32_t u = max(rw.z, step & ~3u); u <= step; ++u) {
+                    const uint4 a = vbuf[u & 3u];
+                    float *o = vrow + 3ll * u;
+                    st_na(o, __uint_as_float(a.x));
+                    st_na(o + 1, __uint_as_float(a.y));
+                    st_na(o + 2, __uint_as_float(a.z));
+                }
+            }
             warp_append(ev == EV_APPEND, P.o, &P.ctrl->o_count, c, f, line, step);
             warp_append(ev == EV_PARK, P.park, &P.ctrl->p_count, c, f, line, step);
             if (ev == EV_STOP) {
@@ -682,21 +796,41 @@ sg_status launch_per_seed(sg_tracer *t, cudaStream_t s)
     return SG_OK;
 }
 
-// The decoupled-lane form runs for the CELL8 layout; SG_KERNEL_LOCKSTEP (and
-// the other layouts) take round_kernel.
-static bool use_async(int kernel, int layout) { return kernel == SG_KERNEL_PERSISTENT && layout == SG_LAYOUT_CELL8; }
+// The decoupled-lane form runs for the CELL8 layout when every brick spans
+// fewer than 2^16 cells per axis (it keeps two of its spans in 16-bit
+// halves); SG_KERNEL_LOCKSTEP, the other layouts and larger bricks take
+// round_kernel, which gives the same bits.
+static bool spans_fit(const DevField &F)
+{
+    for (int a = 0; a < 3; ++a) {
+        const long long last = (long long)F.dims[a] - (long long)(F.B[a] - 1) * F.n[a];
+        if (F.n[a] >= 65536 || last >= 65536) return false;
+    }
+    return true;
+}
 
+static bool use_async(int kernel, int layout, const DevField &F)
+{
+    return kernel == SG_KERNEL_PERSISTENT && layout == SG_LAYOUT_CELL8 && spans_fit(F);
+}
+
+bool decoupled_lanes(const sg_tracer_params *p, const sg_field *f)
+{
+    return use_async(p->kernel, f->desc.layout, f->geom);
+}
+
+// record slot + vertex staging + mbarrier per thread
 template <int DT>
 static size_t async_smem(int block)
 {
-    return (size_t)block * ((Record<DT>::chunks + 1) * 16 + 8);
+    return (size_t)block * ((Record<DT>::chunks + 1) * 16 + 80 + 8);
 }
 
 template <int DT, int LAYOUT>
 static void launch_round_t(const LineParams &P, int grid, int block, int kernel, cudaStream_t s)
 {
     if (kernel == SG_KERNEL_PER_STEP) per_step_kernel<DT, LAYOUT><<<grid, block, 0, s>>>(P);
-    else if (use_async(kernel, LAYOUT)) round_async_kernel<DT><<<grid, block, async_smem<DT>(block), s>>>(P);
+    else if (use_async(kernel, LAYOUT, P.F)) round_async_kernel<DT><<<grid, block, async_smem<DT>(block), s>>>(P);
     else round_kernel<DT, LAYOUT><<<grid, block, 0, s>>>(P);
 }
 
@@ -705,11 +839,11 @@ static void launch_round_t(const LineParams &P, int grid, int block, int kernel,
 // records.  The decoupled-lane kernel asks for the smallest shared part that
 // holds its record slots at the tracer's blocks per SM.
 template <int DT, int LAYOUT>
-static cudaError_t prefer_l1_t(int kernel, int block, int blocks_per_sm)
+static cudaError_t prefer_l1_t(int kernel, int block, int blocks_per_sm, const DevField &F)
 {
     if (kernel == SG_KERNEL_PER_STEP)
         return cudaFuncSetAttribute(per_step_kernel<DT, LAYOUT>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    if (use_async(kernel, LAYOUT)) {
+    if (use_async(kernel, LAYOUT, F)) {
         const size_t per_block = async_smem<DT>(block);
         cudaError_t e = cudaFuncSetAttribute(round_async_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)per_block);
@@ -732,8 +866,8 @@ sg_status prepare_round(sg_tracer *t)
     with_dtype(t->field->desc.dtype, [&](auto D) {
         with_layout(t->field->desc.layout,
                     [&](auto Lay) {
-                        e = prefer_l1_t<decltype(D)::value, decltype(Lay)::value>(t->p.kernel, t->block,
-                                                                                 t->grid / t->ctx->sm_count);
+                        e = prefer_l1_t<decltype(D)::value, decltype(Lay)::value>(
+                            t->p.kernel, t->block, t->grid / t->ctx->sm_count, t->field->geom);
                     });
     });
     SG_CUDA(e);

@@ -59,7 +59,7 @@ LineParams line_params(const sg_tracer *t)
     P.line_len = t->line_len;
     P.line_status = t->line_status;
     P.line_margin = t->line_margin;
-    P.W = (long long)t->p.max_steps + 1;
+    P.W = slab_stride(t->p.max_steps);
     P.n_lines = t->n_lines;
     P.n_seed = t->n_seeds;
     P.n_fwd = t->p.direction == SG_DIR_FORWARD ? t->n_lines : (t->p.direction == SG_DIR_BACKWARD ? 0 : t->n_seeds);
@@ -188,7 +188,7 @@ static size_t tracer_layout(const sg_field *f, const sg_tracer_params *p, int64_
     Carve c{base, 0, 0};
     const int nb = f->nb;
     if (p->mode == SG_STREAMLINE || p->mode == SG_PATHLINE) {
-        const long long W = (long long)p->max_steps + 1;
+        const long long W = slab_stride(p->max_steps);
         const int64_t lc = cap * (p->direction == SG_DIR_BOTH ? 2 : 1);   // line slots
         float *seeds = (float *)c.take(sizeof(float) * 3 * cap);
         float *slab = (float *)c.take(sizeof(float) * 3 * (size_t)W * lc);
@@ -313,12 +313,12 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
     t->block = p->block_size > 0 ? p->block_size : 256;
     // default resident threads per SM (measured on GB300): 512 for the kernels
     // that read every sample through L1, where more particles per SM thrash the
-    // L1 that holds their cell records; for the decoupled-lane kernel, whose
-    // records sit in shared memory and which is bound by instruction issue,
-    // as many as its registers allow: 1024 for FP32 (64 registers), 768 for
-    // the 8-byte formats
-    const bool decoupled = p->kernel == SG_KERNEL_PERSISTENT && f->desc.layout == SG_LAYOUT_CELL8;
-    const int threads_per_sm = decoupled ? (f->desc.dtype == SG_F32 ? 1024 : 768) : 512;
+    // L1 that holds their cell records; 768 for the decoupled-lane kernel,
+    // whose records sit in shared memory and which is built for 3 CTAs of 256
+    // threads per SM (up to 85 registers: at 64 registers, for 1024 threads,
+    // the FP32 form spills and ran 13 % slower)
+    const bool decoupled = decoupled_lanes(p, f);
+    const int threads_per_sm = decoupled ? 768 : 512;
     // round length (measured on GB300): the decoupled kernel gains from longer
     // rounds whose ends are cut short once the queue is empty
     if (t->p.steps_per_round <= 0) t->p.steps_per_round = decoupled ? 256 : 128;
@@ -403,7 +403,7 @@ extern "C" sg_status sg_tracer_upload_seeds(sg_tracer *t, const float *xyz, int6
     if (t->pod_world > 0) {
         // every rank's slab starts at +inf so that the ranks' partial lines
         // merge by an elementwise minimum (each vertex written by one rank)
-        sg_status st = launch_fill_inf(t->slab, 3 * (t->p.max_steps + 1ll) * t->n_lines, s);
+        sg_status st = launch_fill_inf(t->slab, 3 * slab_stride(t->p.max_steps) * t->n_lines, s);
         if (st) return st;
     }
     return launch_upload(t, s);

@@ -175,7 +175,7 @@ __global__ void gather_chunk_kernel(const float *__restrict__ slab, long long W,
 
 sg_status launch_gather_chunk(const sg_tracer *t, long long a, long long b, long long base, float *dst, cudaStream_t s)
 {
-    gather_chunk_kernel<<<t->ctx->sm_count * 8, 256, 0, s>>>(t->slab, (long long)t->p.max_steps + 1, t->line_len,
+    gather_chunk_kernel<<<t->ctx->sm_count * 8, 256, 0, s>>>(t->slab, slab_stride(t->p.max_steps), t->line_len,
                                                               t->offsets, a, b, base, dst);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -259,7 +259,7 @@ sg_status launch_join(sg_tracer *t, int64_t *offsets, float *vertices, int64_t *
         if (offsets) SG_CUDA(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
         return SG_OK;
     }
-    join_gather_kernel<<<t->ctx->sm_count * 8, 256, 0, s>>>(t->slab, (long long)t->p.max_steps + 1, t->line_len,
+    join_gather_kernel<<<t->ctx->sm_count * 8, 256, 0, s>>>(t->slab, slab_stride(t->p.max_steps), t->line_len,
                                                              t->join_off, n, offsets, vertices, seed_vertex);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -287,7 +287,7 @@ sg_status launch_gather_lines(sg_tracer *t, int64_t *offsets, float *vertices, u
 {
     const long long n = t->n_lines;
     int grid = t->ctx->sm_count * 8;
-    gather_lines_kernel<<<grid, 256, 0, s>>>(t->slab, (long long)t->p.max_steps + 1, t->line_len, t->offsets, n,
+    gather_lines_kernel<<<grid, 256, 0, s>>>(t->slab, slab_stride(t->p.max_steps), t->line_len, t->offsets, n,
                                              vertices, t->line_status, status, t->line_margin, margin, offsets);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
@@ -319,6 +319,38 @@ sg_status launch_compact_range(const uint32_t *len, long long n, const float *sl
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }
+
+// ------------------------------------------------------------------ compaction with caller-owned scratch
+
+namespace {
+
+sg_status compact_lines(const float *slab, long long W, const uint32_t *lengths, long long n,
+                        unsigned long long *scratch, int64_t *offsets, float *vertices, cudaStream_t s)
+{
+    const long long nblocks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    int64_t *totals = reinterpret_cast<int64_t *>(scratch + nblocks);
+    if (nblocks > 0) {
+        scan_reduce_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(lengths, n, scratch);
+        SG_CUDA(cudaGetLastError());
+    }
+    scan_blocks_kernel<<<1, SCAN_THREADS, 0, s>>>(scratch, nblocks, totals, offsets, n);
+    SG_CUDA(cudaGetLastError());
+    if (nblocks > 0) {
+        scan_apply_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(lengths, n, scratch, offsets);
+        SG_CUDA(cudaGetLastError());
+        if (vertices) {
+            int dev = 0, sms = 0;
+            SG_CUDA(cudaGetDevice(&dev));
+            SG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            gather_lines_kernel<<<sms * 8, 256, 0, s>>>(slab, W, lengths, offsets, n, vertices, nullptr, nullptr,
+                                                        nullptr, nullptr, nullptr);
+            SG_CUDA(cudaGetLastError());
+        }
+    }
+    return SG_OK;
+}
+
+}  // namespace
 
 // ------------------------------------------------------------------ allocation-free compaction
 //
@@ -371,9 +403,10 @@ extern "C" sg_status sg_lines_compact_static(const float *slab, int64_t max_vert
     unsigned long long *scratch = nullptr;
     sg_status st = static_scratch(&scratch);
     if (st) return st;
-    cudaStream_t s = (cudaStream_t)stream;
+    // the totals go after the chunk sums' maximum extent, as the array is laid out
     const long long n = n_lines;
     const long long nblocks = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    cudaStream_t s = (cudaStream_t)stream;
     int64_t *totals = reinterpret_cast<int64_t *>(scratch + STATIC_MAX_CHUNKS);
     if (nblocks > 0) {
         scan_reduce_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, s>>>(lengths, n, scratch);
@@ -394,4 +427,33 @@ extern "C" sg_status sg_lines_compact_static(const float *slab, int64_t max_vert
         }
     }
     return SG_OK;
+}
+
+extern "C" sg_status sg_lines_compact_scratch_bytes(int64_t n_lines, size_t *bytes)
+{
+    SG_CHECK(n_lines >= 0, SG_ERR_INVALID_ARG, "n_lines must be >= 0");
+    SG_CHECK(bytes != nullptr, SG_ERR_INVALID_ARG, "bytes is NULL");
+    const long long nblocks = (n_lines + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    *bytes = (size_t)(nblocks + 8) * sizeof(unsigned long long);
+    return SG_OK;
+}
+
+extern "C" sg_status sg_lines_compact(const float *slab, int64_t max_vertices_per_line, const uint32_t *lengths,
+                                      int64_t n_lines, void *scratch, size_t scratch_bytes, int64_t *offsets,
+                                      float *vertices, void *stream)
+{
+    SG_CHECK(n_lines >= 0, SG_ERR_INVALID_ARG, "n_lines must be >= 0");
+    SG_CHECK(n_lines < (1ll << 40), SG_ERR_INVALID_ARG, "n_lines too large");
+    SG_CHECK(max_vertices_per_line >= 1 && max_vertices_per_line < (1ll << 28), SG_ERR_INVALID_ARG,
+             "max_vertices_per_line must be in [1, 2^28)");
+    SG_CHECK(offsets != nullptr && scratch != nullptr, SG_ERR_INVALID_ARG, "NULL offsets or scratch");
+    SG_CHECK(((uintptr_t)scratch & 7u) == 0, SG_ERR_INVALID_ARG, "scratch must be 8-byte aligned");
+    SG_CHECK(n_lines == 0 || (lengths != nullptr && (slab != nullptr || vertices == nullptr)), SG_ERR_INVALID_ARG,
+             "NULL input");
+    size_t need = 0;
+    sg_status st = sg_lines_compact_scratch_bytes(n_lines, &need);
+    if (st) return st;
+    SG_CHECK(scratch_bytes >= need, SG_ERR_INVALID_ARG, "scratch of %zu bytes, %zu needed", scratch_bytes, need);
+    return compact_lines(slab, (long long)max_vertices_per_line, lengths, (long long)n_lines,
+                         reinterpret_cast<unsigned long long *>(scratch), offsets, vertices, (cudaStream_t)stream);
 }

@@ -148,7 +148,7 @@ extern "C" sg_status sg_tracer_line_buffers(sg_tracer *t, float **slab, uint32_t
     if (status) *status = t->line_status;
     if (margin) *margin = t->line_margin;
     if (n_lines) *n_lines = t->n_lines;
-    if (max_vertices) *max_vertices = (int64_t)t->p.max_steps + 1;
+    if (max_vertices) *max_vertices = (int64_t)slab_stride(t->p.max_steps);
     t->scanned = false;                  // the caller may rewrite them (a merge across ranks)
     return SG_OK;
 }

@@ -520,7 +520,7 @@ static PathLines path_lines(const sg_tracer *t)
     L.len = t->line_len;
     L.status = t->line_status;
     L.margin = t->line_margin;
-    L.W = (long long)t->p.max_steps + 1;
+    L.W = slab_stride(t->p.max_steps);
     L.n = t->n_lines;
     L.max_steps = (uint32_t)t->p.max_steps;
     L.tie_cells = t->p.tie_cells;

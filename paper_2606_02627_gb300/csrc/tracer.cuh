@@ -17,7 +17,7 @@ struct LineParams {
     uint32_t *line_len;          // vertices per line
     uint8_t *line_status;
     float *line_margin;
-    long long W;                 // max_steps + 1
+    long long W;                 // slab row stride in vertices: max_steps + 1 rounded up to a multiple of 4
     long long n_lines;
     long long n_seed;            // seeds uploaded: line l starts at seed l (l < n_seed) or l - n_seed
     long long n_fwd;             // lines [0, n_fwd) integrate forward, the rest backward (-dt)
@@ -168,6 +168,15 @@ struct sg_tracer {
 };
 
 namespace sg {
+
+// Row stride (vertices) of a streamline or path-line tracer's vertex slab:
+// max_steps + 1 rounded up to a multiple of 4, so that every run of four
+// vertices starting at a multiple of 4 is 48 bytes at a 16-byte boundary.
+inline long long slab_stride(int32_t max_steps) { return ((long long)max_steps + 4) / 4 * 4; }
+
+// Whether a streamline tracer with these parameters runs the decoupled-lane
+// advection kernel on this field.
+bool decoupled_lanes(const sg_tracer_params *p, const sg_field *f);
 
 sg_status launch_upload(sg_tracer *t, cudaStream_t s);
 sg_status launch_join_scan(sg_tracer *t, cudaStream_t s);

@@ -104,3 +104,29 @@ def test_umesh_edge_cases(ctx):
         bad["cell_types"] = m["cell_types"].copy()
         bad["cell_types"][0] = 7
         api.UMesh(ctx, bad)
+
+
+def test_umesh_trace_on_a_side_stream_equals_default_stream(ctx, turb):
+    # the trace, its compaction and its buffers all live on the stream the
+    # caller passes; two traces on two streams at once must not mix
+    from paper_2606_02627_gb300 import api
+    g, F = turb
+    m = inputs.grid_mesh(g, F, kind="hex", jitter=0.15, seed=12)
+    mesh = api.UMesh(ctx, m)
+    seeds = torch.from_numpy(inputs.uniform_seeds(g, 500, 12))
+    dt = 0.5 / oracle.max_speed(F, g.spacing)
+    ref = mesh.trace(seeds, dt, 200)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    a = mesh.trace(seeds, dt, 200, stream=s1)
+    b = mesh.trace(seeds[:250], dt, 150, stream=s2)
+    s1.synchronize()
+    s2.synchronize()
+    for got in (a,):
+        assert torch.equal(got.offsets, ref.offsets)
+        assert torch.equal(got.vertices, ref.vertices)
+        assert torch.equal(got.status, ref.status)
+    alone = mesh.trace(seeds[:250], dt, 150)
+    torch.cuda.synchronize()
+    assert torch.equal(b.offsets, alone.offsets)
+    assert torch.equal(b.vertices, alone.vertices)

@@ -1,9 +1,8 @@
 """The allocation-free compaction entry point (sg_lines_compact_static).
 
 Some callers cannot allocate device memory while they hand work to this
-library: code running while a stream is captured in global mode (cudaMalloc
-is refused then), an in-situ simulation that keeps all of HBM in its own pool,
-or a loop that cannot take the synchronisation cudaMalloc/cudaFree may cause.
+library: an in-situ simulation that keeps all of HBM in its own pool, or a
+loop that cannot take the synchronisation cudaMalloc/cudaFree may cause.
 For them sg_lines_compact_static keeps its scan scratch in a fixed array
 inside the library.  This test calls it through the C ABI and checks its
 output against sg_tracer_get_lines on the same lines, twice in a row (the
