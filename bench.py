@@ -77,6 +77,8 @@ def parse():
                          "a profiler sees every advection-kernel launch")
     ap.add_argument("--once", action="store_true",
                     help="profiling case: one step of the headline form, then print its particle-steps and exit")
+    ap.add_argument("--serve-requests", type=int, default=96,
+                    help="requests of the short serving run whose latency the headline line reports (0: skip)")
     return ap.parse_args()
 
 
@@ -107,24 +109,68 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_step(dtype, tag):
-    """DRAM bytes per particle-step of the advection kernel (tag "async": the
+def counters(dtype, tag):
+    """Per-particle-step counters of the advection kernel (tag "async": the
     decoupled-lane kernel, "lockstep": lanes in lockstep) from the committed
-    ncu summary, or None if it is missing or the kernel changed since."""
+    ncu summary profiles/round_<tag>_<dtype>_traffic.txt, as {name: float},
+    or {} if it is missing or the kernel sources changed since it was taken."""
     p = os.path.join(ROOT, "profiles", f"round_{tag}_{dtype}_traffic.txt")
     if not os.path.exists(p):
-        return None
+        return {}
     kv = {}
     for line in open(p):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if kv.get("kernel_source_hash") != kernel_hash():
-        return None
-    try:
-        return float(kv["dram_bytes_per_particle_step"])
-    except (KeyError, ValueError):
-        return None
+        return {}
+    out = {}
+    for k, v in kv.items():
+        try:
+            out[k] = float(v)
+        except ValueError:
+            pass
+    return out
+
+
+def traffic_per_step(dtype, tag):
+    """DRAM bytes per particle-step (committed ncu summary), or None."""
+    return counters(dtype, tag).get("dram_bytes_per_particle_step")
+
+
+def issue_roofline(steps_per_s, thread_inst_per_step, sm_count, sm_mhz):
+    """Instruction-issue bound of a kernel: each of an SM's 4 schedulers issues
+    at most one warp instruction (32 threads' work) per cycle, so the peak is
+    sm_count x 4 x 32 thread instructions per cycle.  achieved = the kernel's
+    thread instructions per particle-step (ncu) x its particle-steps/s; the
+    fraction counts both idle issue slots and idle lanes of a warp."""
+    peak = sm_count * 4 * 32 * sm_mhz * 1e6
+    achieved = thread_inst_per_step * steps_per_s
+    return achieved / 1e9, peak / 1e9, achieved / peak
+
+
+def copy_rates(dev, nbytes=1 << 31):
+    """Page-locked host <-> device copy rates (GB/s) of one nbytes copy each way, CUDA events."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    out = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        best = None
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            with torch.cuda.stream(s):
+                dst.copy_(src, non_blocking=True)
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name] = nbytes / (best / 1e3) / 1e9
+    del h, d
+    return out
 
 
 class Clocks:
@@ -257,7 +303,7 @@ def run_umesh(args, rank, world, local):
     steps_total = int((lines.lengths().clamp(min=1) - 1).sum().item())
     out = {"metric": "RK4 particle-steps/s (unstructured hexahedra)", "value": steps_total / (ms / 1e3),
            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": "unstructured: 128^3 grid cells of turbulence (seed 1) as 2,097,152 jittered "
                                   "hexahedra, BVH point location, 262144 seeds, RK4 h=0.5 cell, max 1000 steps",
                       "cells": mesh.n_cells, "mesh_build_s": build_s},
@@ -332,7 +378,7 @@ def run_streak(args, rank, world, local):
     h2d = n_slices * n ** 3 * 12
     out = {"metric": "RK4 particle-steps/s (streaklines)", "value": steps / (ms / 1e3), "unit": UNIT,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": f"streaklines: {n_slices} slices of {n}^3 FP32 turbulence (seed 3) streamed from "
                                   f"page-locked host memory, {rakes * per_rake} release points x {per_rake} releases, "
                                   f"RK4 h={args.h} cell", "slots": 3, "bricks": "2x2x2"},
@@ -341,18 +387,18 @@ def run_streak(args, rank, world, local):
     print(json.dumps(out))
 
 
-def run_serve(args, rank, world, local):
+SERVE_WORKLOAD = ("serving: 8 resident fields {64,128,256,512}^3 x {FP32,BF16} turbulence (seeds 4-10), CELL8, "
+                  "4x4x4 bricks; Poisson requests of 100-1M seeds (box/rake), max steps 10-5000, rate = 70 % of "
+                  "the capacity measured on the same requests arriving at once")
+
+
+def serve_workload(ctx, dev, n_requests, h, rank=0, tune=False):
     """Batched serving of interactive seed placement: 8 resident fields ({64,128,256,512}^3 x {FP32, BF16},
-    synthetic turbulence seeds 4-11, CELL8 layout, 4x4x4 bricks), Poisson requests of 100 to 1M seeds (box or
-    rake), max steps 10-5000, admitted into one continuously batched persistent launch by free memory; the
-    arrival rate is 70 % of the capacity measured on the same requests arriving at once."""
+    synthetic turbulence, CELL8 layout, 4x4x4 bricks), Poisson requests of 100 to 1M seeds (box or rake),
+    max steps 10-5000, admitted into one continuously batched persistent launch by free memory; the arrival
+    rate is 70 % of the capacity measured on the same requests arriving at once.  Returns the statistics."""
     import torch
     from paper_2606_02627_gb300 import api, inputs, serving
-    from paper_2606_02627_gb300 import build as _build
-    _build.build()
-    torch.cuda.set_device(local)
-    dev = torch.device(f"cuda:{local}")
-    ctx = api.Context(local)
     fields = []
     seed = 4
     for n in (64, 128, 256, 512):
@@ -360,7 +406,7 @@ def run_serve(args, rank, world, local):
         F = inputs.turbulence_field(g, inputs.turbulence_modes(seed), device=dev)
         probe = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(4, 4, 4), dtype="f32")
         probe.set_global(F)
-        dt = args.h / probe.max_speed()
+        dt = h / probe.max_speed()
         probe.close()
         del probe
         for dtype in ("f32", "bf16"):
@@ -371,19 +417,21 @@ def run_serve(args, rank, world, local):
         seed += 2
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
-    # schedule: the autotuner's pick on the largest FP32 field (a 64k-seed sample, cached per shape)
-    from paper_2606_02627_gb300 import autotune
-    big = fields[6]
-    sample = torch.from_numpy(inputs.uniform_seeds(big.grid, 1 << 16, 99)).to(dev)
-    sched = autotune.tune(ctx, big.field, sample, big.dt, 1000, first=1 << 14,
-                          cache=os.path.join(tempfile.gettempdir(), "streamgb_autotune.json"))
-    torch.cuda.synchronize(dev)
-    torch.cuda.empty_cache()
+    sched = None
+    if tune:
+        # the autotuner's pick on the largest FP32 field (a 64k-seed sample, cached per shape)
+        from paper_2606_02627_gb300 import autotune
+        big = fields[6]
+        sample = torch.from_numpy(inputs.uniform_seeds(big.grid, 1 << 16, 99)).to(dev)
+        sched = autotune.tune(ctx, big.field, sample, big.dt, 1000, first=1 << 14,
+                              cache=os.path.join(tempfile.gettempdir(), "streamgb_autotune.json"))
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info(dev)
     slab = int(min(free * 0.6, 160e9))
     srv = serving.Server(ctx, fields, max_lines=8 << 20, slab_bytes=slab, rounds_per_launch=4,
                          max_requests=1024, schedule=sched)
-    base = serving.make_requests(fields, args.requests, rate_hz=1.0, seed=4 + 1000 * rank)
+    base = serving.make_requests(fields, n_requests, rate_hz=1.0, seed=4 + 1000 * rank)
     # capacity: the same requests all arriving at once
     burst = [serving.Request(r.idx, 0.0, r.field, r.seeds, r.max_steps, r.shape) for r in base]
     srv.serve(burst)
@@ -392,24 +440,44 @@ def run_serve(args, rank, world, local):
     reqs = [serving.Request(r.idx, r.arrival / rate, r.field, r.seeds, r.max_steps, r.shape) for r in base]
     srv.serve(reqs)
     st = serving.summarize(reqs)
-    out = {"metric": "p99 request latency (serving)", "value": st["p99_ms"], "unit": "ms", "n_gpus": 1,
-           "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "serving: 8 resident fields {64,128,256,512}^3 x {FP32,BF16} turbulence, Poisson "
-                                  f"requests ({args.requests}) of 100-1M seeds (box/rake), max steps 10-5000, "
-                                  f"rate = 70 % of measured capacity ({rate:.1f}/s)",
-                      "rounds_per_launch": 4, "slab_pool_bytes": slab, "schedule": sched},
-           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-           "particle_steps_per_s": st["particle_steps_per_s"], "particle_steps": st["particle_steps"],
+    out = {"requests": len(reqs), "rate_per_s": rate, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+           "max_ms": st["max_ms"], "particle_steps_per_s": st["particle_steps_per_s"],
+           "particle_steps": st["particle_steps"], "queue_ms_p99": st["queue_ms_p99"],
            "capacity": {"requests_per_s": len(burst) / cap["makespan_s"],
                         "particle_steps_per_s": cap["particle_steps_per_s"]},
-           "queue_ms_p99": st["queue_ms_p99"]}
+           "rounds_per_launch": 4, "slab_pool_bytes": slab, "schedule": sched or "library default"}
+    del srv, fields
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args, rank, world, local):
+    """The serving workload on its own, with the autotuner's schedule (config 5)."""
+    import torch
+    from paper_2606_02627_gb300 import api
+    from paper_2606_02627_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    ctx = api.Context(local)
+    st = serve_workload(ctx, dev, args.requests, args.h, rank=rank, tune=True)
+    out = {"metric": "p99 request latency (serving)", "value": st["p99_ms"], "unit": "ms", "n_gpus": 1,
+           "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+bf16", "data": "synthetic",
+           "config": {"workload": SERVE_WORKLOAD + f" ({args.requests} requests, {st['rate_per_s']:.1f}/s)",
+                      "rounds_per_launch": st["rounds_per_launch"], "slab_pool_bytes": st["slab_pool_bytes"],
+                      "schedule": st["schedule"]},
+           "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+           "particle_steps_per_s": st["particle_steps_per_s"], "particle_steps": st["particle_steps"],
+           "capacity": st["capacity"], "queue_ms_p99": st["queue_ms_p99"]}
     print(json.dumps(out))
 
 
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.config in ("streak", "umesh") and args.dtype != "f32":
+        raise SystemExit(f"--config {args.config} stores its field in FP32 only (--dtype f32)")
     if args.config == "streak":
         return run_streak(args, rank, world, local)
     if args.config == "serve":
@@ -589,25 +657,47 @@ def main():
     ksteps = tr.total_steps(stream=stream)
     hbm, peak_kind = peaks()
     bps = GATHER_BYTES[args.dtype]
-    achieved = ksteps * bps / (kms / 1e3) / 1e9
+    k_rate = ksteps / (kms / 1e3)                       # particle-steps/s of the advection kernel alone
     tag = "async" if args.kernel == "persistent" and args.layout == "cell8" else "lockstep"
-    tps = traffic_per_step(args.dtype, tag)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+    cnt = counters(args.dtype, tag)
+    tps = cnt.get("dram_bytes_per_particle_step")
+    tips = cnt.get("thread_inst_per_particle_step")
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz") or 2070.0
+    gather = ksteps * bps / (kms / 1e3) / 1e9
+    roofline = {"bound": "issue", "achieved": None, "peak": None, "unit": "G thread-instructions/s", "frac": None,
                 "traffic": (tps * ksteps / launches) if tps else None,
                 "kernel": ("round_async_kernel (persistent advection, decoupled lanes)"
-                           if args.kernel == "persistent" and args.layout == "cell8"
-                           else "round_kernel (persistent advection, lanes in lockstep)"),
-                "peak_source": f"{peak_kind} hbm_gbs",
-                "model": f"gather bytes: 4 samples x 8 corners x 3 comps x elem + 12 B vertex = {bps} B "
-                         f"per particle-step (L1/L2 hits counted at HBM price)",
+                           if tag == "async" else "round_kernel (persistent advection, lanes in lockstep)"),
+                "peak_source": f"{sm_count} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz (median SM clock "
+                               "under load in this run): one warp instruction per scheduler per cycle",
+                "model": "thread instructions per particle-step (ncu smsp__thread_inst_executed.sum over every "
+                         "advection launch of one trace, committed in profiles/) x the kernel's particle-steps/s",
                 "kernel_ms_per_launch": kms / launches, "launches": launches,
-                "particle_steps_per_launch": ksteps / launches}
+                "particle_steps_per_launch": ksteps / launches, "kernel_particle_steps_per_s": k_rate,
+                "thread_inst_per_particle_step": tips,
+                "threads_per_warp_inst": cnt.get("threads_per_warp_inst"),
+                "gather_model": {"achieved": gather, "peak": hbm, "unit": "GB/s", "frac": gather / hbm,
+                                 "peak_source": f"{peak_kind} hbm_gbs",
+                                 "model": f"4 samples x 8 corners x 3 comps x elem + 12 B vertex = {bps} B per "
+                                          "particle-step (hits in the lane's record slot, L1 and L2 counted at "
+                                          "HBM price)"},
+                "dram": ({"bytes_per_particle_step": tps, "achieved": tps * k_rate / 1e9, "peak": hbm,
+                          "unit": "GB/s", "frac": tps * k_rate / 1e9 / hbm, "peak_source": f"{peak_kind} hbm_gbs"}
+                         if tps else None)}
+    if tips:
+        a, pk, fr = issue_roofline(k_rate, tips, sm_count, sm_mhz)
+        roofline.update(achieved=a, peak=pk, frac=fr)
 
     # e2e through the C ABI: seeds from pinned host, CSR lines to pinned host (copy overlapping the next
     # step), inside the timed region
     ems, _, etot_all, d2h = timed(fld, tr, 2, max(1, args.steps), seeds_pin, host_out=True)
     e2e = {"value": etot_all / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(seeds_pin.numel() * 4),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": ems}
+    # the host link it runs on: one 2 GiB page-locked copy each way (the step's D2H copy overlaps the next
+    # step's trace, so the step takes about max(trace, D2H copy) plus the pipeline's fill and drain)
+    e2e.update(copy_rates(dev))
+    e2e["d2h_ms_per_step"] = d2h / (e2e["d2h_gbs"] * 1e9) * 1e3
     del tr, fld
     torch.cuda.empty_cache()
 
@@ -630,6 +720,13 @@ def main():
         variants[f"{args.dtype}_{args.kernel}"] = {"value": value, "ms_per_step": ms, "particle_steps": tot,
                                                    "field_storage": args.dtype, "kernel": args.kernel}
 
+    serve = None
+    if args.serve_requests > 0:
+        # continuous batching of interactive seed placement (config 5's recipe, a shorter request stream):
+        # p50 / p99 request latency beside the throughput
+        serve = serve_workload(ctx, dev, args.serve_requests, args.h, rank=rank, tune=False)
+        serve["workload"] = SERVE_WORKLOAD + f" ({args.serve_requests} requests)"
+
     cpu = None
     if rank == 0:
         F_host = F.cpu().numpy()
@@ -646,12 +743,12 @@ def main():
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+               "vs_baseline": None, "dtype": args.dtype, "data": "synthetic", "config": config,
                "particle_steps_per_step": tot_all, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": None, "clocks": clocks, "variants": variants}
+               "serving": serve, "gpu_launches": None, "clocks": clocks, "variants": variants}
         # kernels of ours per timed step: set_global (2-3), upload (1), prepare (1), bin (4) + rounds x (1 + 4),
-        # scan (3), gather (1)
-        out["gpu_launches"] = int(args.steps * (3 + 1 + 1 + 4 + launches * 5 + 3 + 1))
+        # park_rest (1), scan (3), gather (1)
+        out["gpu_launches"] = int(args.steps * (3 + 1 + 1 + 4 + launches * 5 + 1 + 3 + 1))
         print(json.dumps(out))
     if dist:
         dist.barrier()

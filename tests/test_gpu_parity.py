@@ -169,6 +169,29 @@ def test_bricked_equals_single_brick_bit_exact(ctx, dtype, layout):
             assert torch.equal(o.vertices, out[0].vertices)
 
 
+def test_fp32_layouts_and_kernels_give_the_same_bits(ctx):
+    # FP32 samples are stored as given in every layout, and every kernel
+    # interpolates them with the same operations in the same order: the
+    # global float3 array (per-seed kernel), LINEAR and TILED4 bricks (lanes in
+    # lockstep) and CELL8 records (decoupled lanes, and lockstep) give the same
+    # lines bit for bit
+    g = inputs.cube_grid(45)
+    F = inputs.turbulence_field(g, inputs.turbulence_modes(13, n_modes=64, kmax=3)).numpy()
+    seeds = inputs.uniform_seeds(g, 3000, 13)
+    dt = 0.5 / oracle.max_speed(F, g.spacing)
+    runs = []
+    for kernel, layout, bricks in (("per_seed", "global", (1, 1, 1)), ("persistent", "linear", (3, 2, 2)),
+                                   ("persistent", "tiled4", (2, 2, 2)), ("persistent", "cell8", (3, 3, 1)),
+                                   ("lockstep", "cell8", (1, 1, 1))):
+        fld = make_field(ctx, g, F, bricks=bricks, layout=layout)
+        _, lines = run(ctx, fld, seeds, dt, 500, kernel=kernel)
+        runs.append(lines)
+    for other in runs[1:]:
+        assert torch.equal(other.offsets, runs[0].offsets)
+        assert torch.equal(other.vertices, runs[0].vertices)
+        assert torch.equal(other.status, runs[0].status)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16", "fx21"])
 def test_decoupled_lanes_equal_lockstep_bit_exact(ctx, dtype):
     # CELL8 fields: the persistent kernel runs each lane's stages on its own
