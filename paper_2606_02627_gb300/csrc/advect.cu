@@ -208,10 +208,15 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
     unsigned parity = 0, waited = 0;
     int c[3] = {0, 0, 0}, q[3] = {0, 0, 0};               // P0 and the current sample point
     float f[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};
-    // k1 and k2 (k2 + k3 after stage 2), the step factor: x and y as packed
-    // pairs, z alone
-    f32x2 k1xy = 0, k23xy = 0, dsxy = 0;
-    float k1z = 0.f, k23z = 0.f, dsz = 0.f;
+    // k1 and k2 (k2 + k3 after stage 2) and the step factor, per component.
+    // The stage arithmetic and this state are scalar: with the x and y
+    // components carried across the unrolled stages as packed register pairs,
+    // about one step in 500 came out one unit in the last place away from
+    // rk4_bricked's result; scalar they give its bits, at the same speed.  The
+    // interpolation keeps its packed pairs.
+    float k1x = 0.f, k1y = 0.f, k1z = 0.f;
+    float k23x = 0.f, k23y = 0.f, k23z = 0.f;
+    float dsx = 0.f, dsy = 0.f, dsz = 0.f;
     uint32_t line = 0, step = 0, stage = 0;
     // steps the lane may take before its step horizon or the round's step
     // budget stops it: min(horizon - step, steps_per_round - steps this round)
@@ -271,7 +276,8 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
                         q[a] = c[a];
                         g[a] = f[a];
                     }
-                    dsxy = pk2(ds[0], ds[1]);
+                    dsx = ds[0];
+                    dsy = ds[1];
                     dsz = ds[2];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
@@ -342,7 +348,7 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
         }
         // the four stages; iteration S runs stage S: sample, k = v dt/h, and
         // the next point P0 + k1/2, P0 + k2/2, P0 + k3 or P'
-#pragma unroll 1
+#pragma unroll
         for (int S = 0; S < 4; ++S) {
             if (go && stage == (uint32_t)S) {
                 Record<DT> R;
@@ -350,35 +356,33 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
                 for (int k = 0; k < NCH; ++k) R.r[k] = my_slot[k];
                 bool bad_flag;                       // FX21: a corner's stored flag
                 const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad_flag);
-                const f32x2 vxy = pk2(v.x, v.y);
-                const f32x2 kxy = mul2(vxy, dsxy);
-                const float kz = __fmul_rn(v.z, dsz);
-                float dxy_x, dxy_y, dz;              // offset of the next point from P0
+                const float kx = __fmul_rn(v.x, dsx), ky = __fmul_rn(v.y, dsy), kz = __fmul_rn(v.z, dsz);
+                float dx, dy, dz;                    // offset of the next point from P0
                 if (S == 0) {
-                    k1xy = kxy;
+                    k1x = kx;
+                    k1y = ky;
                     k1z = kz;
                 } else if (S == 1) {
-                    k23xy = kxy;
+                    k23x = kx;
+                    k23y = ky;
                     k23z = kz;
                 } else if (S == 2) {
-                    k23xy = add2(k23xy, kxy);
+                    k23x = __fadd_rn(k23x, kx);
+                    k23y = __fadd_rn(k23y, ky);
                     k23z = __fadd_rn(k23z, kz);
                 }
                 if (S < 3) {
                     const float w = S < 2 ? 0.5f : 1.0f;   // P1, P2 = P0 + k/2; P3 = P0 + k3
-                    const float2 wk = upk2(mul2(pk2(w, w), kxy));
-                    dxy_x = wk.x;
-                    dxy_y = wk.y;
-                    dz = w * kz;
+                    dx = __fmul_rn(w, kx);
+                    dy = __fmul_rn(w, ky);
+                    dz = __fmul_rn(w, kz);
                 } else {
-                    const float2 fin = upk2(mul2(add2(add2(k1xy, kxy), mul2(pk2(2.0f, 2.0f), k23xy)),
-                                                 pk2(1.0f / 6.0f, 1.0f / 6.0f)));
-                    dxy_x = fin.x;
-                    dxy_y = fin.y;
+                    dx = __fmul_rn(__fadd_rn(__fadd_rn(k1x, kx), __fmul_rn(2.0f, k23x)), 1.0f / 6.0f);
+                    dy = __fmul_rn(__fadd_rn(__fadd_rn(k1y, ky), __fmul_rn(2.0f, k23y)), 1.0f / 6.0f);
                     dz = __fmul_rn(__fadd_rn(__fadd_rn(k1z, kz), __fmul_rn(2.0f, k23z)), 1.0f / 6.0f);
                 }
-                locate(f[0], dxy_x, c[0], q[0], g[0]);
-                locate(f[1], dxy_y, c[1], q[1], g[1]);
+                locate(f[0], dx, c[0], q[0], g[0]);
+                locate(f[1], dy, c[1], q[1], g[1]);
                 locate(f[2], dz, c[2], q[2], g[2]);
                 const bool in_box = (unsigned)(q[0] - box_lo[0]) <= box_span[0] &&
                                     (unsigned)(q[1] - box_lo[1]) <= box_span[1] &&
@@ -389,13 +393,10 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
                 bool maybe_bad;
                 if constexpr (DT == SG_FX21) {
                     maybe_bad = bad_flag;
-                    if (S == 0) {
-                        const float2 sq = upk2(mul2(vxy, vxy));
-                        s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
-                    }
+                    if (S == 0)
+                        s2 = __fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z));
                 } else {
-                    const float2 sq = upk2(mul2(vxy, vxy));
-                    s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
+                    s2 = __fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z));
                     maybe_bad = !(s2 < INFINITY);
                 }
                 const float e2 = (DT == SG_F32) ? __fmul_ru(P.eps, P.eps) : e2min;
