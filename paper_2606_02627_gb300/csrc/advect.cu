@@ -139,6 +139,27 @@ __global__ void __launch_bounds__(256) round_kernel(const __grid_constant__ Line
 // takes at least ~100 cycles: well over a second in all).
 constexpr unsigned COPY_WAIT_PASSES = 1u << 24;
 
+// Shared memory of the decoupled-lane kernel, per thread, in this order over
+// the block: every storage type interpolates an FP32 record (6 chunks of 16 B)
+// in the lane's slot, followed by a 16-byte pad; the 8-byte formats' 64-byte
+// records land in a separate area and are decoded into the slot once, when
+// the copy lands (that area's fifth chunk holds the brick scale and the eps^2
+// threshold); the vertex staging area holds four 16-byte vertices, then the
+// line's slab row pointer, the first vertex this lane writes and a brick
+// extent; then one 8-byte mbarrier.  Every stride is a multiple of 16 bytes
+// and an odd number of 16-byte chunks, so that the 16-byte accesses of eight
+// consecutive lanes fall in eight different bank groups.
+template <int DT>
+struct AsyncLayout {
+    static constexpr int NCH = Record<SG_F32>::chunks;                 // chunks of the FP32 record
+    static constexpr int RAW = Record<DT>::chunks;                     // chunks one copy brings
+    static constexpr unsigned SLOT = (NCH + 1) * 16;
+    static constexpr unsigned LAND = (DT == SG_F32) ? 0u : (RAW + 1) * 16;
+    static constexpr unsigned VBUF = 80;
+    static constexpr unsigned BAR = 8;
+    static constexpr unsigned PER_THREAD = SLOT + LAND + VBUF + BAR;
+};
+
 // The same round as round_kernel for the CELL8 layout, with the lanes of a
 // warp no longer waiting for one another at each sample.  In round_kernel
 // every one of the four samples of a step is a load that the whole warp
@@ -175,21 +196,17 @@ constexpr unsigned COPY_WAIT_PASSES = 1u << 24;
 template <int DT>
 __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_constant__ LineParams P)
 {
-    constexpr int NCH = Record<DT>::chunks;
-    constexpr unsigned SLOT = (NCH + 1) * 16;              // bytes per lane slot
-    // vertex staging per lane: four 16-byte vertices, then the line's slab
-    // row pointer and the first vertex this lane writes for its particle
-    // (read only when vertices leave, so they need no registers)
-    constexpr unsigned VBUF = 80;
-    // [blockDim][SLOT bytes] record slots, [blockDim][VBUF bytes] vertex
-    // staging, then blockDim barriers
+    using L = AsyncLayout<DT>;
+    constexpr int NCH = L::NCH, RAW = L::RAW;
+    constexpr unsigned SLOT = L::SLOT, LAND = L::LAND, VBUF = L::VBUF;
     extern __shared__ uint4 slots[];
     const unsigned tid = threadIdx.x, nthr = blockDim.x;
     const unsigned lane = tid & 31;
     uint4 *my_slot = slots + tid * (SLOT / 16);
-    uint4 *vbuf = slots + nthr * (SLOT / 16) + tid * (VBUF / 16);
-    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + nthr * ((SLOT + VBUF) / 16)) + tid);
-    const uint32_t slot = smem_addr(my_slot);
+    uint4 *my_land = slots + nthr * (SLOT / 16) + tid * (LAND / 16);
+    uint4 *vbuf = slots + nthr * ((SLOT + LAND) / 16) + tid * (VBUF / 16);
+    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + nthr * ((SLOT + LAND + VBUF) / 16)) + tid);
+    const uint32_t slot = smem_addr(DT == SG_F32 ? my_slot : my_land);   // where a copy lands
     mbar_init(bar, 1);
     mbar_init_fence();
     __syncwarp();
@@ -222,6 +239,7 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
     // budget stops it: min(horizon - step, steps_per_round - steps this round)
     int left = 0;
     uint32_t held = 0xffffffffu;                           // cell of the record in (or on its way to) the slot
+    bool rec_bad = false;                                  // FX21: a corner of the slot's record is flagged
     BrickRef<DT> br;
     br.data = nullptr;
     br.scale = 1.0f;
@@ -237,14 +255,12 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
     // shell: a stage point there needs neither the EXIT nor the HALO test
     int box_lo[3] = {0, 0, 0};
     unsigned box_span[3] = {0u, 0u, 0u};
-    // |v|^2 at or above e2min (before the brick scale) means |v| >= eps
-    float e2min = 0.f;
 
     // the cell of sample point q within the brick's records
     auto cell_of = [&]() { return (uint32_t)((q[2] * F.C[1] + q[1]) * F.C[0] + q[0] + cbase); };
     // copy the record of `cell` into the slot
     auto fetch = [&](uint32_t cell) {
-        bulk_copy_arrive(slot, br.data + (long long)cell * record_elems<DT>(), NCH * 16u, bar);
+        bulk_copy_arrive(slot, br.data + (long long)cell * record_elems<DT>(), RAW * 16u, bar);
         inflight = true;
         held = cell;
         pending = true;
@@ -287,9 +303,10 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
                         box_span[a] = hi >= lo ? (unsigned)(hi - lo) : 0u;
                         if (hi < lo) box_lo[a] = 0x7fffffff;   // empty: every point takes the full tests
                     }
-                    {
-                        const float e = (DT == SG_F32) ? P.eps : __fdiv_ru(P.eps, br.scale);
-                        e2min = __fmul_ru(e, e);
+                    if constexpr (DT != SG_F32) {
+                        // |v|^2 at or above e2min (before the brick scale) means |v| >= eps
+                        const float e = __fdiv_ru(P.eps, br.scale);
+                        my_land[RAW] = make_uint4(__float_as_uint(__fmul_ru(e, e)), __float_as_uint(br.scale), 0u, 0u);
                     }
                     {
                         const unsigned long long row =
@@ -318,6 +335,30 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
                 parity ^= 1u;
                 pending = false;
                 inflight = false;
+                if constexpr (DT != SG_F32) {
+                    // decode the landed record once into the FP32 slot, one x face at a
+                    // time: corner (dx, dy, dz) is sample dx of raw chunk dy + 2 dz, and
+                    // its component a goes to f32_record_index(a, dx, dy, dz)
+                    unsigned flags = 0u;
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        float3 cr[4];                // (dy, dz) = (0,0), (1,0), (0,1), (1,1)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint4 w = my_land[j];
+                            const uint2 e = dx ? make_uint2(w.z, w.w) : make_uint2(w.x, w.y);
+                            cr[j] = decode_elem<DT>(e);
+                            flags |= elem_flag<DT>(e);
+                        }
+                        my_slot[dx] = make_uint4(__float_as_uint(cr[0].x), __float_as_uint(cr[2].x),
+                                                 __float_as_uint(cr[1].x), __float_as_uint(cr[3].x));
+                        my_slot[2 + dx] = make_uint4(__float_as_uint(cr[0].y), __float_as_uint(cr[2].y),
+                                                     __float_as_uint(cr[1].y), __float_as_uint(cr[3].y));
+                        my_slot[4 + dx] = make_uint4(__float_as_uint(cr[0].z), __float_as_uint(cr[2].z),
+                                                     __float_as_uint(cr[1].z), __float_as_uint(cr[3].z));
+                    }
+                    rec_bad = flags != 0u;
+                }
             } else if (++waited >= COPY_WAIT_PASSES) {
                 // the particle is dropped and the call fails; the warp takes
                 // no other particle while this lane's barrier may still complete
@@ -351,11 +392,12 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
 #pragma unroll
         for (int S = 0; S < 4; ++S) {
             if (go && stage == (uint32_t)S) {
-                Record<DT> R;
+                Record<SG_F32> R;
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) R.r[k] = my_slot[k];
-                bool bad_flag;                       // FX21: a corner's stored flag
-                const float3 v = interp_record<DT>(R, g[0], g[1], g[2], bad_flag);
+                bool bad_flag;                       // a non-finite corner (FX21: a flagged one)
+                const float3 v = interp_record<SG_F32>(R, g[0], g[1], g[2], bad_flag);
+                if constexpr (DT == SG_FX21) bad_flag = rec_bad;
                 const float kx = __fmul_rn(v.x, dsx), ky = __fmul_rn(v.y, dsy), kz = __fmul_rn(v.z, dsz);
                 float dx, dy, dz;                    // offset of the next point from P0
                 if (S == 0) {
@@ -399,14 +441,15 @@ __global__ void __launch_bounds__(256, 3) round_async_kernel(const __grid_consta
                     s2 = __fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z));
                     maybe_bad = !(s2 < INFINITY);
                 }
-                const float e2 = (DT == SG_F32) ? __fmul_ru(P.eps, P.eps) : e2min;
+                float e2 = 0.f;
+                if (S == 0) e2 = (DT == SG_F32) ? __fmul_ru(P.eps, P.eps) : __uint_as_float(my_land[RAW].x);
                 if (maybe_bad || (S == 0 && !(s2 >= e2)) || !in_box) {
                     // the tests in full (rare): a sample that may not be finite, a
                     // speed that may be below eps, a point near the domain or
                     // brick boundary
                     const bool bad = (DT == SG_FX21) ? bad_flag : bad3(v);
                     float sp = sqrtf(s2);
-                    if (DT != SG_F32) sp = __fmul_rn(sp, br.scale);
+                    if (DT != SG_F32) sp = __fmul_rn(sp, __uint_as_float(my_land[RAW].y));
                     if (bad) {
                         st = SG_LINE_NANFIELD;
                     } else if (S == 0 && sp < P.eps) {
@@ -820,11 +863,11 @@ bool decoupled_lanes(const sg_tracer_params *p, const sg_field *f)
     return use_async(p->kernel, f->desc.layout, f->geom);
 }
 
-// record slot + vertex staging + mbarrier per thread
+// dynamic shared memory of the decoupled-lane kernel (AsyncLayout)
 template <int DT>
 static size_t async_smem(int block)
 {
-    return (size_t)block * ((Record<DT>::chunks + 1) * 16 + 80 + 8);
+    return (size_t)block * AsyncLayout<DT>::PER_THREAD;
 }
 
 template <int DT, int LAYOUT>
