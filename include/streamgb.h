@@ -278,8 +278,10 @@ sg_status sg_tracer_params_default(sg_tracer_params *p);
 
 /* Device bytes of a tracer for up to `capacity` seeds (streamlines) or
  * release points (streaklines): particle queues, the per-line vertex slabs
- * (capacity * (max_steps+1) * 12 B for streamlines), per-line lengths and
- * status, and the scan scratch of the compaction. */
+ * (capacity * W * 12 B for streamlines and path lines, W = max_steps + 1
+ * rounded up to a multiple of 4, so that runs of four vertices are 48 bytes at
+ * a 16-byte boundary), per-line lengths and status, and the scan scratch of
+ * the compaction. */
 sg_status sg_tracer_required_bytes(const sg_context *ctx, const sg_field *f, const sg_tracer_params *p,
                                    int64_t capacity, size_t *bytes);
 
@@ -433,7 +435,8 @@ sg_status sg_tracer_pod_import(sg_tracer *t, const void *records, int64_t count,
 sg_status sg_tracer_pod_queued(const sg_tracer *t, int64_t *count);
 
 /* Device pointers of the tracer's line buffers inside its workspace (each
- * nullable): slab (n_lines x max_vertices x 3 floats), length (u32),
+ * nullable): slab (n_lines x max_vertices x 3 floats; max_vertices is the
+ * row stride, max_steps + 1 rounded up to a multiple of 4), length (u32),
  * status (u8), margin (f32).  For merging the ranks' partial lines; the next
  * sg_tracer_get_lines rescans them. */
 sg_status sg_tracer_line_buffers(sg_tracer *t, float **slab, uint32_t **length, uint8_t **status, float **margin,
@@ -528,7 +531,8 @@ sg_status sg_seeds_box(const double lo[3], const double hi[3], int64_t n, uint64
  * types may differ (each lane decodes its own request's type). */
 typedef struct {
     int64_t max_lines;       /* line slots: lines of admitted, not yet released requests */
-    int64_t slab_bytes;      /* vertex slab pool ((max_steps+1) * 12 B per line of a request) */
+    int64_t slab_bytes;      /* vertex slab pool: W * 12 B per line of a request, W =
+                                max_steps + 1 rounded up to a multiple of 4      */
     int32_t max_requests;    /* request table entries (<= 1048576) */
     int32_t max_fields;      /* distinct fields used by requests (<= 64) */
     int32_t max_bricks;      /* bricks summed over those fields (<= 65536) */

@@ -172,99 +172,88 @@ __global__ void __launch_bounds__(256) batch_round_kernel(const __grid_constant_
 }
 
 // The same round with the lanes of a warp decoupled (CELL8 layout), as the
-// tracer's round_async_kernel: each lane keeps the cell record of its current
-// sample point in its own shared-memory slot (an FP32 record of 6 chunks of
-// 16 B plus one chunk of padding: the 8-byte formats use 4 chunks of it),
-// fetches another with one TMA bulk copy completing on its own mbarrier, and
-// runs one RK4 stage per pass; the storage type of each lane's request
-// selects the decode.  Stage arithmetic as rk4_bricked's.
-constexpr int BATCH_SLOT_CHUNKS = Record<SG_F32>::chunks + 1;
+// tracer's round_async_kernel: a pass runs up to four RK4 stages, unrolled
+// (iteration s runs stage s for the lanes at stage s whose record is at
+// hand); each lane keeps the FP32 cell record of its current sample point in
+// a shared-memory slot and fetches another with one TMA bulk copy completing
+// on its own mbarrier; the 8-byte formats' records land in a separate area
+// and are decoded into the slot once, with the storage type of the lane's own
+// request; vertices are staged and leave as 48-byte runs.  Stage arithmetic as
+// rk4_bricked's, so a request's lines are the tracer's bits.
+//
+// Shared memory per thread: the FP32 slot (6 chunks) and a pad holding the
+// brick's first owned cell and two extents; the landing area (4 chunks) and a
+// pad holding the eps^2 threshold, brick scale and step cap; the vertex
+// staging (4 chunks) and a pad holding the slab row pointer, the first vertex
+// this lane writes and the third extent; one mbarrier.  Strides of 7, 5 and 5
+// chunks keep eight consecutive lanes' 16-byte accesses in different banks.
+struct BatchLayout {
+    static constexpr int NCH = Record<SG_F32>::chunks;
+    static constexpr unsigned SLOT = (NCH + 1) * 16;
+    static constexpr unsigned LAND = (Record<SG_F16>::chunks + 1) * 16;
+    static constexpr unsigned VBUF = 80;
+    static constexpr unsigned PER_THREAD = SLOT + LAND + VBUF + 8;
+};
 // Consecutive passes a lane may wait for one record copy (each pass takes at
 // least ~100 cycles: well over a second in all), as in the tracer's kernel.
 constexpr unsigned BATCH_COPY_WAIT_PASSES = 1u << 24;
 
-__device__ __forceinline__ float3 interp_slot(int dtype, const uint4 *slot, float fx, float fy, float fz, bool &bad)
+template <int DT>
+__device__ __forceinline__ void decode_face(const uint4 *land, int dx, float3 cr[4], unsigned &flags)
 {
-    switch (dtype) {
-    case SG_BF16: {
-        Record<SG_BF16> R;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) R.r[k] = slot[k];
-        return interp_record<SG_BF16>(R, fx, fy, fz, bad);
-    }
-    case SG_F16: {
-        Record<SG_F16> R;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) R.r[k] = slot[k];
-        return interp_record<SG_F16>(R, fx, fy, fz, bad);
-    }
-    case SG_FX21: {
-        Record<SG_FX21> R;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) R.r[k] = slot[k];
-        return interp_record<SG_FX21>(R, fx, fy, fz, bad);
-    }
-    default: {
-        Record<SG_F32> R;
-#pragma unroll
-        for (int k = 0; k < Record<SG_F32>::chunks; ++k) R.r[k] = slot[k];
-        return interp_record<SG_F32>(R, fx, fy, fz, bad);
-    }
+    for (int j = 0; j < 4; ++j) {
+        const uint4 w = land[j];
+        const uint2 e = dx ? make_uint2(w.z, w.w) : make_uint2(w.x, w.y);
+        cr[j] = decode_elem<DT>(e);
+        flags |= elem_flag<DT>(e);
     }
 }
 
-__global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant__ BatchParams P)
+__global__ void __launch_bounds__(256, 3) batch_async_kernel(const __grid_constant__ BatchParams P)
 {
-    extern __shared__ uint4 slots[];                       // [blockDim][7 chunks], then blockDim barriers
+    using L = BatchLayout;
+    constexpr int NCH = L::NCH;
+    extern __shared__ uint4 slots[];
     const unsigned tid = threadIdx.x, nthr = blockDim.x;
     const unsigned lane = tid & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const uint4 *my_slot = slots + tid * BATCH_SLOT_CHUNKS;
-    const uint32_t bar = smem_addr(reinterpret_cast<uint64_t *>(slots + BATCH_SLOT_CHUNKS * nthr) + tid);
-    const uint32_t slot = smem_addr(my_slot);
+    uint4 *my_slot = slots + tid * (L::SLOT / 16);
+    uint4 *my_land = slots + nthr * (L::SLOT / 16) + tid * (L::LAND / 16);
+    uint4 *vbuf = slots + nthr * ((L::SLOT + L::LAND) / 16) + tid * (L::VBUF / 16);
+    const uint32_t bar =
+        smem_addr(reinterpret_cast<uint64_t *>(slots + nthr * ((L::SLOT + L::LAND + L::VBUF) / 16)) + tid);
+    const uint32_t slot_f32 = smem_addr(my_slot), slot_raw = smem_addr(my_land);
     mbar_init(bar, 1);
     mbar_init_fence();
     __syncwarp();
 
-    const uint32_t q_count = P.ctrl->q_count;
+    const uint32_t *q_count_p = &P.ctrl->q_count;
     bool active = false, pending = false;
     bool inflight = false;                                 // a copy may still land in the slot
-    bool drained = q_count == 0;
-    uint32_t drain_left = P.drain_steps >= 0x20000000u ? 0xffffffffu : P.drain_steps * 4u;   // 4 passes a step
+    bool drained = __ldg(q_count_p) == 0;
+    uint32_t drain_left = P.drain_steps;                   // one pass per step
     unsigned parity = 0, waited = 0;
     int c[3] = {0, 0, 0}, q[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};
-    // k1-k3 and ds: x and y as packed pairs, z alone
-    f32x2 k1xy = 0, k2xy = 0, k3xy = 0, dsxy = 0;
-    float k1z = 0.f, k2z = 0.f, k3z = 0.f, dsz = 0.f;
-    uint32_t line = 0, step = 0, stage = 0, r = 0, max_steps = 0;
-    int left = 0;                        // steps before max_steps or the round's step budget stops the lane
-    uint32_t held = 0xffffffffu, wanted = 0;
+    float k1x = 0.f, k1y = 0.f, k1z = 0.f;
+    float k23x = 0.f, k23y = 0.f, k23z = 0.f;
+    float dsx = 0.f, dsy = 0.f, dsz = 0.f;
+    uint32_t line = 0, step = 0, stage = 0, r = 0;
     int dtype = SG_F32;
-    float eps = 0.f;
-    float *vp = nullptr;                 // where the line's next vertex goes
-    const ReqDev *R = P.reqs;
-    BrickAny br;
-    br.data = nullptr;
-    br.scale = 1.0f;
-    for (int a = 0; a < 3; ++a) br.lo[a] = br.hi[a] = 0;
-    // as in the tracer's kernel: a stage point in the box needs neither the
-    // EXIT nor the HALO test, and |v|^2 >= e2min means |v| >= eps
+    int left = 0;                        // steps before max_steps or the round's step budget stops the lane
+    uint32_t held = 0xffffffffu;         // cell of the record in (or on its way to) the slot
+    bool rec_bad = false;                // FX21: a corner of the slot's record is flagged
+    const char *bdata = nullptr;         // the brick's records
+    int cbase = 0, C0 = 0, C1 = 0;       // record index of cell q: (q.z C1 + q.y) C0 + q.x + cbase
     int box_lo[3] = {0, 0, 0};
     unsigned box_span[3] = {0u, 0u, 0u};
-    float e2min = 0.f;
 
-    auto cell_of = [&]() {
-        const DevField &F = R->F;
-        const int sx = q[0] - br.lo[0] + 1, sy = q[1] - br.lo[1] + 1, sz = q[2] - br.lo[2] + 1;
-        return (uint32_t)((sz * F.C[1] + sy) * F.C[0] + sx);
-    };
+    auto cell_of = [&]() { return (uint32_t)((q[2] * C1 + q[1]) * C0 + q[0] + cbase); };
     auto fetch = [&](uint32_t cell) {
-        const int nch = dtype == SG_F32 ? Record<SG_F32>::chunks : Record<SG_F16>::chunks;
-        bulk_copy_arrive(slot, reinterpret_cast<const uint4 *>(br.data) + (long long)cell * nch, nch * 16u, bar);
+        const uint32_t bytes = dtype == SG_F32 ? (uint32_t)(NCH * 16) : (uint32_t)(Record<SG_F16>::chunks * 16);
+        bulk_copy_arrive(dtype == SG_F32 ? slot_f32 : slot_raw, bdata + (long long)cell * bytes, bytes, bar);
         inflight = true;
-        held = 0xffffffffu;
-        wanted = cell;
+        held = cell;
         pending = true;
         waited = 0;
     };
@@ -277,18 +266,20 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
             uint32_t base = 0;
             if ((int)lane == leader) base = atomicAdd(&P.ctrl->q_head, (uint32_t)__popc(need));
             base = __shfl_sync(SG_FULL_MASK, base, leader);
+            const uint32_t q_count = __ldg(q_count_p);
             if (base + (uint32_t)__popc(need) >= q_count) drained = true;
             if (!active) {
-                const uint32_t my = base + __popc(need & lt);
+                const uint32_t my = base + __popc(need & ((1u << lane) - 1u));
                 if (my < q_count) {
                     load_particle(P.q + my, c, f, line, step);
                     r = P.line_req[line];
-                    R = P.reqs + r;
+                    const ReqDev *R = P.reqs + r;
                     dtype = R->dtype;
-                    max_steps = R->max_steps;
-                    eps = R->eps;
-                    vp = P.slab + R->slab_base + ((long long)(line - R->line_base) * R->W + step + 1) * 3;
-                    brick_any(R->F, dtype, c, br);
+                    const uint32_t max_steps = R->max_steps;
+                    const DevField &F = R->F;
+                    BrickAny br;
+                    brick_any(F, dtype, c, br);
+                    bdata = br.data;
                     float ds[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
@@ -296,9 +287,9 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
                         q[a] = c[a];
                         g[a] = f[a];
                     }
-                    dsxy = pk2(ds[0], ds[1]);
+                    dsx = ds[0];
+                    dsy = ds[1];
                     dsz = ds[2];
-                    const DevField &F = R->F;
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const int lo = max(br.lo[a] - 1, 0);
@@ -306,9 +297,21 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
                         box_lo[a] = hi >= lo ? lo : 0x7fffffff;   // empty: every point takes the full tests
                         box_span[a] = hi >= lo ? (unsigned)(hi - lo) : 0u;
                     }
+                    C0 = F.C[0];
+                    C1 = F.C[1];
+                    cbase = -(((br.lo[2] - 1) * C1 + (br.lo[1] - 1)) * C0 + (br.lo[0] - 1));
                     {
-                        const float e = dtype == SG_F32 ? eps : __fdiv_ru(eps, br.scale);
-                        e2min = __fmul_ru(e, e);
+                        // |v|^2 at or above the threshold (before the brick scale) means |v| >= eps
+                        const float e = dtype == SG_F32 ? R->eps : __fdiv_ru(R->eps, br.scale);
+                        my_land[4] = make_uint4(__float_as_uint(__fmul_ru(e, e)), __float_as_uint(br.scale),
+                                                max_steps, 0u);
+                        const unsigned long long row = reinterpret_cast<unsigned long long>(
+                            P.slab + R->slab_base + (long long)(line - R->line_base) * R->W * 3);
+                        const uint32_t sp0 = (uint32_t)(br.hi[0] - br.lo[0]), sp1 = (uint32_t)(br.hi[1] - br.lo[1]);
+                        vbuf[4] = make_uint4((uint32_t)row, (uint32_t)(row >> 32), step + 1,
+                                             (uint32_t)(br.hi[2] - br.lo[2]));
+                        my_slot[NCH] = make_uint4((uint32_t)br.lo[0], (uint32_t)br.lo[1], (uint32_t)br.lo[2],
+                                                  sp0 | (sp1 << 16));
                     }
                     left = step >= max_steps ? 0 : (int)min(max_steps - step, P.steps_per_round);
                     active = true;
@@ -324,10 +327,28 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
         bool gave_up = false;
         if (pending) {
             if (mbar_done(bar, parity)) {
-                held = wanted;
                 parity ^= 1u;
                 pending = false;
                 inflight = false;
+                if (dtype != SG_F32) {
+                    // decode the landed record once into the FP32 slot, one x face at
+                    // a time, with the lane's own storage type
+                    unsigned flags = 0u;
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        float3 cr[4];                // (dy, dz) = (0,0), (1,0), (0,1), (1,1)
+                        if (dtype == SG_BF16) decode_face<SG_BF16>(my_land, dx, cr, flags);
+                        else if (dtype == SG_F16) decode_face<SG_F16>(my_land, dx, cr, flags);
+                        else decode_face<SG_FX21>(my_land, dx, cr, flags);
+                        my_slot[dx] = make_uint4(__float_as_uint(cr[0].x), __float_as_uint(cr[2].x),
+                                                 __float_as_uint(cr[1].x), __float_as_uint(cr[3].x));
+                        my_slot[2 + dx] = make_uint4(__float_as_uint(cr[0].y), __float_as_uint(cr[2].y),
+                                                     __float_as_uint(cr[1].y), __float_as_uint(cr[3].y));
+                        my_slot[4 + dx] = make_uint4(__float_as_uint(cr[0].z), __float_as_uint(cr[2].z),
+                                                     __float_as_uint(cr[1].z), __float_as_uint(cr[3].z));
+                    }
+                    rec_bad = flags != 0u;
+                }
             } else if (++waited >= BATCH_COPY_WAIT_PASSES) {
                 atomicOr(&P.ctrl->err, CTRL_ERR_TIMEOUT);
                 active = false;
@@ -339,97 +360,165 @@ __global__ void __launch_bounds__(256) batch_async_kernel(const __grid_constant_
 
         int ev = EV_NONE, st = SG_LINE_ACTIVE;
         float margin = INFINITY;
-        bool run = active && !pending;
-        if (run && stage == 0 && left <= 0) {
-            if (step >= max_steps) {
+        bool go = active && !pending;
+        bool run_done = false;                       // this pass completed vertex 4j+3 of the row
+        if (go && stage == 0 && left <= 0) {
+            if (step >= my_land[4].z) {
                 ev = EV_STOP;
                 st = SG_LINE_MAXSTEPS;
             } else {
                 ev = EV_APPEND;                   // the round's step budget is spent
             }
-            run = false;
+            go = false;
         }
-        if (run) {
-            const DevField &F = R->F;
-            bool bad_flag;                          // FX21: a corner's stored flag
-            const float3 v = interp_slot(dtype, my_slot, g[0], g[1], g[2], bad_flag);
-            const f32x2 vxy = pk2(v.x, v.y);
-            const float2 sq = upk2(mul2(vxy, vxy));
-            const float s2 = __fadd_rn(__fadd_rn(sq.x, sq.y), __fmul_rn(v.z, v.z));
-            const f32x2 kxy = mul2(vxy, dsxy);
-            const float kz = __fmul_rn(v.z, dsz);
-            const bool last = stage == 3;
-            const float w = stage < 2 ? 0.5f : 1.0f;
-            const float2 fin = upk2(mul2(add2(add2(k1xy, kxy), mul2(pk2(2.0f, 2.0f), add2(k2xy, k3xy))),
-                                         pk2(1.0f / 6.0f, 1.0f / 6.0f)));
-            const float finz = __fmul_rn(__fadd_rn(__fadd_rn(k1z, kz), __fmul_rn(2.0f, __fadd_rn(k2z, k3z))), 1.0f / 6.0f);
-            const float2 wk = upk2(mul2(pk2(w, w), kxy));
-            locate(f[0], last ? fin.x : wk.x, c[0], q[0], g[0]);
-            locate(f[1], last ? fin.y : wk.y, c[1], q[1], g[1]);
-            locate(f[2], last ? finz : w * kz, c[2], q[2], g[2]);
-            k1xy = stage == 0 ? kxy : k1xy;
-            k2xy = stage == 1 ? kxy : k2xy;
-            k3xy = stage == 2 ? kxy : k3xy;
-            k1z = stage == 0 ? kz : k1z;
-            k2z = stage == 1 ? kz : k2z;
-            k3z = stage == 2 ? kz : k3z;
-            const bool in_box = (unsigned)(q[0] - box_lo[0]) <= box_span[0] &&
-                                (unsigned)(q[1] - box_lo[1]) <= box_span[1] &&
-                                (unsigned)(q[2] - box_lo[2]) <= box_span[2];
-            const bool maybe_bad = dtype == SG_FX21 ? bad_flag : !(s2 < INFINITY);
-            if (maybe_bad || (stage == 0 && !(s2 >= e2min)) || !in_box) {
-                // the tests in full (rare)
-                const bool bad = dtype == SG_FX21 ? bad_flag : bad3(v);
-                float sp = sqrtf(s2);
-                if (dtype != SG_F32) sp = __fmul_rn(sp, br.scale);
-                if (bad) {
-                    st = SG_LINE_NANFIELD;
-                } else if (stage == 0 && sp < eps) {
-                    margin = (eps - sp) / eps;
-                    st = SG_LINE_STAGNANT;
-                } else if (!in_domain(F, q, g)) {
-                    margin = out_dist(F, q, g);
-                    st = SG_LINE_EXIT;
-                } else if (!last && ((unsigned)(q[0] - br.lo[0] + 1) > (unsigned)(F.S[0] - 2) ||
-                                     (unsigned)(q[1] - br.lo[1] + 1) > (unsigned)(F.S[1] - 2) ||
-                                     (unsigned)(q[2] - br.lo[2] + 1) > (unsigned)(F.S[2] - 2))) {
-                    st = SG_LINE_HALO;
-                }
-            }
-            bool go = st == SG_LINE_ACTIVE;
-            if (!go) ev = EV_STOP;
-            if (go && last) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    c[a] = q[a];
-                    f[a] = g[a];
+        for (int S = 0; S < 4; ++S) {
+            if (go && stage == (uint32_t)S) {
+                Record<SG_F32> Rc;
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) Rc.r[k] = my_slot[k];
+                bool bad_flag;
+                const float3 v = interp_record<SG_F32>(Rc, g[0], g[1], g[2], bad_flag);
+                const float kx = __fmul_rn(v.x, dsx), ky = __fmul_rn(v.y, dsy), kz = __fmul_rn(v.z, dsz);
+                float dx, dy, dz;                    // offset of the next point from P0
+                if (S == 0) {
+                    k1x = kx;
+                    k1y = ky;
+                    k1z = kz;
+                } else if (S == 1) {
+                    k23x = kx;
+                    k23y = ky;
+                    k23z = kz;
+                } else if (S == 2) {
+                    k23x = __fadd_rn(k23x, kx);
+                    k23y = __fadd_rn(k23y, ky);
+                    k23z = __fadd_rn(k23z, kz);
                 }
-                ++step;
-                --left;
-                st_na(vp, fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0]));
-                st_na(vp + 1, fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1]));
-                st_na(vp + 2, fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2]));
-                vp += 3;
-                const bool out = (unsigned)(c[0] - br.lo[0]) >= (unsigned)(br.hi[0] - br.lo[0]) ||
-                                 (unsigned)(c[1] - br.lo[1]) >= (unsigned)(br.hi[1] - br.lo[1]) ||
-                                 (unsigned)(c[2] - br.lo[2]) >= (unsigned)(br.hi[2] - br.lo[2]);
-                if (left <= 0 || out) {
+                if (S < 3) {
+                    const float w = S < 2 ? 0.5f : 1.0f;   // P1, P2 = P0 + k/2; P3 = P0 + k3
+                    dx = __fmul_rn(w, kx);
+                    dy = __fmul_rn(w, ky);
+                    dz = __fmul_rn(w, kz);
+                } else {
+                    dx = __fmul_rn(__fadd_rn(__fadd_rn(k1x, kx), __fmul_rn(2.0f, k23x)), 1.0f / 6.0f);
+                    dy = __fmul_rn(__fadd_rn(__fadd_rn(k1y, ky), __fmul_rn(2.0f, k23y)), 1.0f / 6.0f);
+                    dz = __fmul_rn(__fadd_rn(__fadd_rn(k1z, kz), __fmul_rn(2.0f, k23z)), 1.0f / 6.0f);
+                }
+                locate(f[0], dx, c[0], q[0], g[0]);
+                locate(f[1], dy, c[1], q[1], g[1]);
+                locate(f[2], dz, c[2], q[2], g[2]);
+                const bool in_box = (unsigned)(q[0] - box_lo[0]) <= box_span[0] &&
+                                    (unsigned)(q[1] - box_lo[1]) <= box_span[1] &&
+                                    (unsigned)(q[2] - box_lo[2]) <= box_span[2];
+                const float s2 = __fadd_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)), __fmul_rn(v.z, v.z));
+                const bool maybe_bad = dtype == SG_FX21 ? rec_bad : !(s2 < INFINITY);
+                if (maybe_bad || (S == 0 && !(s2 >= __uint_as_float(my_land[4].x))) || !in_box) {
+                    // the tests in full (rare)
+                    const ReqDev *R = P.reqs + r;
+                    const DevField &F = R->F;
+                    const bool bad = dtype == SG_FX21 ? rec_bad : bad3(v);
+                    float sp = sqrtf(s2);
+                    if (dtype != SG_F32) sp = __fmul_rn(sp, __uint_as_float(my_land[4].y));
+                    const float eps = R->eps;
+                    if (bad) {
+                        st = SG_LINE_NANFIELD;
+                    } else if (S == 0 && sp < eps) {
+                        margin = (eps - sp) / eps;
+                        st = SG_LINE_STAGNANT;
+                    } else if (!in_domain(F, q, g)) {
+                        margin = out_dist(F, q, g);
+                        st = SG_LINE_EXIT;
+                    } else if (S < 3) {
+                        const uint4 bl = my_slot[NCH];
+                        if ((unsigned)(q[0] - (int)bl.x + 1) > (unsigned)(F.S[0] - 2) ||
+                            (unsigned)(q[1] - (int)bl.y + 1) > (unsigned)(F.S[1] - 2) ||
+                            (unsigned)(q[2] - (int)bl.z + 1) > (unsigned)(F.S[2] - 2))
+                            st = SG_LINE_HALO;
+                    }
+                }
+                if (st != SG_LINE_ACTIVE) {
+                    ev = EV_STOP;
                     go = false;
-                    if (step >= max_steps) {
-                        ev = EV_STOP;
-                        st = SG_LINE_MAXSTEPS;
-                    } else if (out) {
-                        ev = EV_APPEND;
+                } else if (S == 3) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        c[a] = q[a];
+                        f[a] = g[a];
+                    }
+                    ++step;
+                    --left;
+                    {
+                        const DevField &F = P.reqs[r].F;
+                        vbuf[step & 3u] = make_uint4(__float_as_uint(fmaf(F.spacing[0], (float)c[0] + f[0], F.origin[0])),
+                                                     __float_as_uint(fmaf(F.spacing[1], (float)c[1] + f[1], F.origin[1])),
+                                                     __float_as_uint(fmaf(F.spacing[2], (float)c[2] + f[2], F.origin[2])),
+                                                     0u);
+                    }
+                    run_done = (step & 3u) == 3u;
+                    stage = 0;
+                    const uint4 bl = my_slot[NCH];
+                    const bool out = (unsigned)(c[0] - (int)bl.x) >= (bl.w & 0xffffu) ||
+                                     (unsigned)(c[1] - (int)bl.y) >= (bl.w >> 16) ||
+                                     (unsigned)(c[2] - (int)bl.z) >= vbuf[4].w;
+                    if (left <= 0 || out) {
+                        go = false;
+                        if (step >= my_land[4].z) {
+                            ev = EV_STOP;
+                            st = SG_LINE_MAXSTEPS;
+                        } else {
+                            ev = EV_APPEND;           // another brick, or the round's step budget is spent
+                        }
+                    }
+                } else {
+                    stage = S + 1;
+                }
+                if (go) {
+                    const uint32_t next = cell_of();
+                    if (next != held) {
+                        fetch(next);
+                        go = false;
                     }
                 }
             }
-            stage = last ? 0 : stage + 1;
-            const uint32_t next = cell_of();
-            if (go && next != held) fetch(next);
+        }
+        if (run_done) {
+            const uint4 rw = vbuf[4];
+            float *vrow = reinterpret_cast<float *>(((unsigned long long)rw.y << 32) | rw.x);
+            if (step - 3u >= rw.z) {
+                // the row's run 4j .. 4j+3 is this lane's: 48 bytes at a 16-byte boundary
+                uint4 *o = reinterpret_cast<uint4 *>(vrow + 3ll * (step - 3u));
+                const uint4 a = vbuf[0], b = vbuf[1];
+                st_na4(o, make_uint4(a.x, a.y, a.z, b.x));
+                const uint4 cc = vbuf[2];
+                st_na4(o + 1, make_uint4(b.y, b.z, cc.x, cc.y));
+                const uint4 d = vbuf[3];
+                st_na4(o + 2, make_uint4(cc.z, d.x, d.y, d.z));
+            } else {
+                for (uint32_t u = rw.z; u <= step; ++u) {
+                    const uint4 a = vbuf[u & 3u];
+                    float *o = vrow + 3ll * u;
+                    st_na(o, __uint_as_float(a.x));
+                    st_na(o + 1, __uint_as_float(a.y));
+                    st_na(o + 2, __uint_as_float(a.z));
+                }
+            }
         }
         if (__any_sync(SG_FULL_MASK, ev != EV_NONE)) {
+            if (ev != EV_NONE && (step & 3u) != 3u) {
+                // the particle leaves: the staged vertices of its unfinished run
+                const uint4 rw = vbuf[4];
+                float *vrow = reinterpret_cast<float *>(((unsigned long long)rw.y << 32) | rw.x);
+                for (uint32_t u = max(rw.z, step & ~3u); u <= step; ++u) {
+                    const uint4 a = vbuf[u & 3u];
+                    float *o = vrow + 3ll * u;
+                    st_na(o, __uint_as_float(a.x));
+                    st_na(o + 1, __uint_as_float(a.y));
+                    st_na(o + 2, __uint_as_float(a.z));
+                }
+            }
             warp_append(ev == EV_APPEND, P.o, &P.ctrl->o_count, c, f, line, step);
             if (ev == EV_STOP) {
+                const ReqDev *R = P.reqs + r;
                 P.line_len[line] = step + 1;
                 P.line_status[line] = stop_code_t(st, margin, R->tie_cells, R->tie_eps_rel);
                 P.line_margin[line] = margin;
@@ -696,7 +785,7 @@ static sg_status check_desc(const sg_batch_desc *d)
     return SG_OK;
 }
 
-static size_t batch_async_smem(int block) { return (size_t)block * (BATCH_SLOT_CHUNKS * 16 + 8); }
+static size_t batch_async_smem(int block) { return (size_t)block * BatchLayout::PER_THREAD; }
 
 static BatchParams batch_params(const sg_batch *b)
 {
@@ -963,7 +1052,7 @@ extern "C" sg_status sg_batch_submit(sg_batch *b, sg_field *f, const float *xyz,
         set_error("the request table is full");
         return SG_ERR_OOM;
     }
-    const long long W = (long long)p->max_steps + 1;
+    const long long W = slab_stride(p->max_steps);    // rows of whole 4-vertex runs
     long long line_base = 0, slab_off = 0;
     const long long slab_len = (long long)n * W * 3;
     if (n > 0 && !b->lines.alloc(n, 1, &line_base)) {

@@ -50,7 +50,7 @@ __device__ __forceinline__ void line_dtc(const LineParams &P, long long line, fl
 
 // One request of a batch (device copy).  Its lines occupy the global line
 // slots [line_base, line_base + n_lines); its vertex slabs start at float
-// slab_base of the batch's slab pool, max_steps + 1 vertices per line.
+// slab_base of the batch's slab pool, W vertices per line.
 struct ReqDev {
     DevField F;                  // slot 0 of the request's field
     float dtc[3];
@@ -58,7 +58,7 @@ struct ReqDev {
     float tie_cells;
     float tie_eps_rel;
     uint32_t max_steps;
-    uint32_t W;                  // max_steps + 1
+    uint32_t W;                  // slab row stride in vertices (max_steps + 1 rounded up to a multiple of 4)
     long long slab_base;
     uint32_t line_base;
     uint32_t n_lines;

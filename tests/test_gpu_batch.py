@@ -112,7 +112,10 @@ def test_alone_equals_mixed_with_continuous_admission(ctx, fields):
 
 def test_admission_refuses_then_accepts(ctx, fields):
     rf = fields[0][0]
-    b = batch(ctx, max_lines=3000, slab_bytes=2000 * 101 * 12 + 4096)
+    # a request's vertex rows hold max_steps + 1 = 101 vertices rounded up to a
+    # multiple of 4: the pool fits the first request, not both
+    row = (100 + 4) // 4 * 4
+    b = batch(ctx, max_lines=3000, slab_bytes=2000 * row * 12 + 4096)
     s1 = inputs.uniform_seeds(rf.grid, 2000, 1)
     s2 = inputs.uniform_seeds(rf.grid, 1500, 2)
     r1 = b.submit(rf.field, s1, rf.dt, 100)
