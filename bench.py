@@ -77,6 +77,9 @@ def parse():
                          "a profiler sees every advection-kernel launch")
     ap.add_argument("--once", action="store_true",
                     help="profiling case: one step of the headline form, then print its particle-steps and exit")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="run the headline on the library's default structure and schedule instead of the "
+                         "autotuner's pick (layout, bricks, brick window, threads, CTAs/SM, steps per round, drain)")
     ap.add_argument("--serve-requests", type=int, default=96,
                     help="requests of the short serving run whose latency the headline line reports (0: skip)")
     return ap.parse_args()
@@ -557,12 +560,13 @@ def main():
     seeds_dev = torch.from_numpy(seeds_np).to(dev)
     seeds_pin = torch.from_numpy(seeds_np).pin_memory()
 
-    def make(dtype, layout, kernel):
+    def make(dtype, layout, kernel, bricks=(4, 4, 4), extra=None):
         fld = api.Field(ctx, grid.dims, grid.origin, grid.spacing,
-                        bricks=(1, 1, 1) if layout == "global" else (4, 4, 4), dtype=dtype, layout=layout)
+                        bricks=(1, 1, 1) if layout == "global" else tuple(bricks), dtype=dtype, layout=layout)
         fld.set_global(F, stream=stream)
-        tr = api.Tracer(ctx, fld, capacity=args.seeds, dt=dt, max_steps=args.max_steps, kernel=kernel,
-                        **(sched if kernel in ("persistent", "lockstep") else {}))
+        kw = dict(sched) if kernel in ("persistent", "lockstep") else {}
+        kw.update(extra or {})
+        tr = api.Tracer(ctx, fld, capacity=args.seeds, dt=dt, max_steps=args.max_steps, kernel=kernel, **kw)
         return fld, tr
 
     # dt from the FP32 field's largest speed: every step is at most h cells
@@ -628,8 +632,27 @@ def main():
     except Exception:
         pass
 
-    # headline: the chosen storage type and persistent kernel
-    fld, tr = make(args.dtype, args.layout, args.kernel)
+    # headline: the chosen storage type and persistent kernel, on the structure and schedule the autotuner
+    # picks for this workload (successive halving over layouts, brick shapes, brick windows and schedules on
+    # growing prefixes of the same seeds, up to all of them)
+    tuned = None
+    head_bricks, head_extra, head_layout = (4, 4, 4), {}, args.layout
+    if not args.no_tune and not args.schedule and args.kernel == "persistent" and not args.once:
+        from paper_2606_02627_gb300 import autotune
+        t0 = time.time()
+        # the workload fixes the decomposition (4x4x4 bricks): layouts, brick windows and schedules are tuned
+        choice = autotune.tune_structure(ctx, F, grid, args.dtype, seeds_dev, dt, args.max_steps, first=1 << 16,
+                                         structs=autotune.structures(64, bricks=((4, 4, 4),)),
+                                         cache=os.path.join(tempfile.gettempdir(), f"streamgb_tune_{os.getpid()}.json"),
+                                         stream=stream)
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        head_layout, head_bricks = choice["layout"], tuple(choice["bricks"])
+        head_extra = dict(choice["schedule"], brick_window=choice["brick_window"])
+        tuned = dict(choice, seconds=round(time.time() - t0, 1))
+        config.update(layout=head_layout, bricks="x".join(map(str, head_bricks)))
+    config["schedule"] = tuned or {"schedule": "library default" if not args.schedule else sched}
+    fld, tr = make(args.dtype, head_layout, args.kernel, head_bricks, head_extra)
     if args.once:
         # one whole step: field store, seeds, rounds, and the CSR gathered into device buffers
         one_step(fld, tr, None, None, None, seeds_dev)
@@ -658,7 +681,7 @@ def main():
     hbm, peak_kind = peaks()
     bps = GATHER_BYTES[args.dtype]
     k_rate = ksteps / (kms / 1e3)                       # particle-steps/s of the advection kernel alone
-    tag = "async" if args.kernel == "persistent" and args.layout == "cell8" else "lockstep"
+    tag = "async" if args.kernel == "persistent" and head_layout == "cell8" else "lockstep"
     cnt = counters(args.dtype, tag)
     tps = cnt.get("dram_bytes_per_particle_step")
     tips = cnt.get("thread_inst_per_particle_step")

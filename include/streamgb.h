@@ -251,7 +251,8 @@ typedef struct {
     float tie_eps_rel;     /* tie threshold for STAGNANT (relative)                 */
     int32_t inject_steps;  /* streaklines: particles released per release point     */
     /* schedule of the persistent kernel (0 = default) */
-    int32_t block_size;    /* threads per CTA (multiple of 32, <= 1024)              */
+    int32_t block_size;    /* threads per CTA (multiple of 32, <= 256: the kernels'
+                              register budget)                                   */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent grid                     */
     int32_t steps_per_round; /* steps a particle may take in one round before it is
                                 re-queued in its own brick (0 = default: 256 for the
@@ -270,6 +271,16 @@ typedef struct {
                               default (128 for the decoupled-lane kernel, no limit
                               otherwise); negative = no limit                      */
     int32_t direction;     /* SG_DIR_* (streamlines; 0 = forward)                   */
+    int32_t brick_window;  /* rounds policy of the persistent kernels (streamlines):
+                              0 = every round advances the particles of all
+                              bricks; w > 0 = brick-major: a round advances only
+                              the particles of w consecutive bricks (round-robin
+                              over the bricks, skipping empty ones) and carries
+                              the others to the next round, so that a round's
+                              field accesses stay within w bricks (L2 locality
+                              for fields larger than L2).  The lines are the same
+                              bits either way.  Ignored by SG_KERNEL_PER_STEP and
+                              by partitioned tracers.                            */
 } sg_tracer_params;
 
 /* Fills p with the defaults (streamline, persistent kernel, eps 1e-6,

@@ -46,7 +46,8 @@ class sg_tracer_params(ctypes.Structure):
                 ("max_steps", ctypes.c_int32), ("eps", ctypes.c_float), ("tie_cells", ctypes.c_float),
                 ("tie_eps_rel", ctypes.c_float), ("inject_steps", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("steps_per_round", ctypes.c_int32),
-                ("max_rounds", ctypes.c_int32), ("drain_steps", ctypes.c_int32), ("direction", ctypes.c_int32)]
+                ("max_rounds", ctypes.c_int32), ("drain_steps", ctypes.c_int32), ("direction", ctypes.c_int32),
+                ("brick_window", ctypes.c_int32)]
 
 
 class sg_batch_desc(ctypes.Structure):

@@ -191,7 +191,7 @@ def seeds_box(lo, hi, n: int, seed: int, stream_id: int = 0, device="cuda", stre
 
 def tracer_params(dt, max_steps=1000, mode="streamline", kernel="persistent", eps=1e-6, tie_cells=1e-3,
                   tie_eps_rel=1e-3, inject_steps=1, block_size=0, blocks_per_sm=0, steps_per_round=0,
-                  max_rounds=0, drain_steps=0, direction="forward") -> L.sg_tracer_params:
+                  max_rounds=0, drain_steps=0, direction="forward", brick_window=0) -> L.sg_tracer_params:
     p = L.sg_tracer_params()
     call("sg_tracer_params_default", ctypes.byref(p))
     p.mode = {"streamline": L.SG_STREAMLINE, "streakline": L.SG_STREAKLINE, "pathline": L.SG_PATHLINE}[mode]
@@ -208,6 +208,7 @@ def tracer_params(dt, max_steps=1000, mode="streamline", kernel="persistent", ep
     p.max_rounds = int(max_rounds)
     p.drain_steps = int(drain_steps)
     p.direction = DIRECTIONS[direction] if isinstance(direction, str) else int(direction)
+    p.brick_window = int(brick_window)
     return p
 
 

@@ -151,11 +151,15 @@ static sg_status check_params(const sg_field *f, const sg_tracer_params *p)
              "bad mode %d", p->mode);
     SG_CHECK(p->dt > 0.0 && p->dt < 1e30, SG_ERR_INVALID_ARG, "dt must be > 0");
     SG_CHECK(p->eps >= 0.0f, SG_ERR_INVALID_ARG, "eps must be >= 0");
-    SG_CHECK(p->block_size >= 0 && p->block_size <= 1024 && p->block_size % 32 == 0, SG_ERR_INVALID_ARG,
-             "block_size must be a multiple of 32 in [0, 1024]");
+    // every streamline kernel is built for at most 256 threads per CTA (its
+    // register budget): a larger block would fail at launch, inside the
+    // capture of the round loop's graph
+    SG_CHECK(p->block_size >= 0 && p->block_size <= 256 && p->block_size % 32 == 0, SG_ERR_INVALID_ARG,
+             "block_size must be a multiple of 32 in [0, 256]");
     SG_CHECK(p->blocks_per_sm >= 0 && p->blocks_per_sm <= 32, SG_ERR_INVALID_ARG, "blocks_per_sm in [0, 32]");
     SG_CHECK(p->steps_per_round >= 0, SG_ERR_INVALID_ARG, "steps_per_round must be >= 0");
     SG_CHECK(p->max_rounds >= 0, SG_ERR_INVALID_ARG, "max_rounds must be >= 0");
+    SG_CHECK(p->brick_window >= 0, SG_ERR_INVALID_ARG, "brick_window must be >= 0");
     SG_CHECK(p->direction >= SG_DIR_FORWARD && p->direction <= SG_DIR_BOTH, SG_ERR_INVALID_ARG, "bad direction %d",
              p->direction);
     if (p->mode == SG_STREAMLINE) {
@@ -451,6 +455,7 @@ static sg_status build_graph(sg_tracer *t)
                 st = cuda_error(e, "body capture");
             } else {
                 st = launch_round(t, cs);
+                if (st == SG_OK) st = launch_carry(t, cs);
                 if (st == SG_OK) st = launch_bin(t, t->o, &t->ctrl->o_count, cs, true, (unsigned long long)h, 1);
                 cudaGraph_t b2 = nullptr;
                 e2 = cudaStreamEndCapture(cs, &b2);
@@ -472,18 +477,27 @@ static sg_status build_graph(sg_tracer *t)
     return SG_OK;
 }
 
+// Round cap of a call that advances particles up to `horizon` steps: every
+// round advances each particle of its brick window by at least one step, no
+// particle starts a call below step 0 (a call that the round cap stopped
+// leaves particles behind the horizon), and a sweep over the bricks takes
+// ceil(bricks / window) rounds, so (horizon + 2) sweeps finish a call; the cap
+// only guards against a fault unless the caller sets max_rounds.
+static uint64_t round_guard(const sg_tracer *t, uint32_t horizon)
+{
+    const uint64_t w = (uint64_t)(t->p.brick_window > 0 ? t->p.brick_window : t->nb);
+    const uint64_t sweeps = ((uint64_t)t->nb + w - 1) / w;
+    return ((uint64_t)horizon + 2) * (sweeps > 0 ? sweeps : 1);
+}
+
 static sg_status run_call(sg_tracer *t, uint32_t horizon, uint32_t n_steps, cudaStream_t s)
 {
     if (!t->graph_ready) {
         sg_status st = build_graph(t);
         if (st) return st;
     }
-    // every round advances each remaining particle by at least one step, and
-    // no particle starts a call below step 0 (a call that the round cap
-    // stopped leaves particles behind the horizon), so horizon + 2 rounds
-    // finish a call; this cap only guards against a fault
     (void)n_steps;
-    uint64_t cap = (uint64_t)horizon + 2;
+    uint64_t cap = round_guard(t, horizon);
     if (t->p.max_rounds > 0 && (uint64_t)t->p.max_rounds < cap) cap = (uint64_t)t->p.max_rounds;
     if (cap > 0xffffffffull) cap = 0xffffffffull;
     sg_status st = launch_prepare_call(t, horizon, (uint32_t)cap, s);
@@ -553,7 +567,7 @@ extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int3
         const uint32_t n = target > t->horizon ? target - t->horizon : 0;
         t->horizon = target;
         (void)n;
-        uint64_t cap = (uint64_t)target + 2;
+        uint64_t cap = round_guard(t, target);
         if (t->p.max_rounds > 0 && (uint64_t)t->p.max_rounds < cap) cap = (uint64_t)t->p.max_rounds;
         if (cap > 0xffffffffull) cap = 0xffffffffull;
         st = launch_prepare_call(t, target, (uint32_t)cap, s);
@@ -570,6 +584,8 @@ extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int3
             st = launch_round(t, s);
             if (st) break;
             if ((ce = cudaEventRecord(e1, s)) != cudaSuccess) { st = cuda_error(ce, "cudaEventRecord"); break; }
+            st = launch_carry(t, s);
+            if (st) break;
             st = launch_bin(t, t->o, &t->ctrl->o_count, s, false, 0ull, 1);
             if (st) break;
             if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) { st = cuda_error(ce, "cudaEventSynchronize"); break; }
@@ -578,7 +594,7 @@ extern "C" sg_status sg_tracer_trace_timed(sg_tracer *t, double *kernel_ms, int3
             total += ms;
             if (round_ms && round_particles && n_launch < max_records) {
                 round_ms[n_launch] = ms;
-                round_particles[n_launch] = c.q_count;
+                round_particles[n_launch] = c.q_count - c.win_start;
             }
             ++n_launch;
         }

@@ -778,8 +778,8 @@ static sg_status check_desc(const sg_batch_desc *d)
     SG_CHECK(d->max_bricks >= 1 && d->max_bricks <= 65536, SG_ERR_INVALID_ARG, "max_bricks out of range");
     SG_CHECK(d->layout == SG_LAYOUT_LINEAR || d->layout == SG_LAYOUT_TILED4 || d->layout == SG_LAYOUT_CELL8,
              SG_ERR_INVALID_ARG, "a batch samples bricked layouts");
-    SG_CHECK(d->block_size >= 0 && d->block_size <= 1024 && d->block_size % 32 == 0, SG_ERR_INVALID_ARG,
-             "bad block_size");
+    SG_CHECK(d->block_size >= 0 && d->block_size <= 256 && d->block_size % 32 == 0, SG_ERR_INVALID_ARG,
+             "block_size must be a multiple of 32 in [0, 256]");
     SG_CHECK(d->blocks_per_sm >= 0 && d->blocks_per_sm <= 32, SG_ERR_INVALID_ARG, "bad blocks_per_sm");
     SG_CHECK(d->steps_per_round >= 0, SG_ERR_INVALID_ARG, "bad steps_per_round");
     return SG_OK;

@@ -131,7 +131,15 @@ struct Ctrl {
     uint32_t max_rounds;
     uint32_t horizon;        // a particle advances while step < horizon
     uint32_t last_rounds;    // rounds of the last finished call
-    uint32_t pad[7];
+    // rounds policy: with window > 0 a round advances only the particles of
+    // `window` consecutive bricks (round-robin from win_lo, skipping empty
+    // ones); the queue then holds q_total records, of which [win_start,
+    // q_count) are the round's and the rest are carried to the next round
+    uint32_t window;
+    uint32_t win_lo;
+    uint32_t win_start;
+    uint32_t q_total;
+    uint32_t pad[3];
 };
 
 enum { CTRL_ERR_ROUND_LIMIT = 1u, CTRL_ERR_TIMEOUT = 2u };

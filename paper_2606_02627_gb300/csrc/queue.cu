@@ -121,18 +121,75 @@ __global__ void bin_scatter_kernel(BinArgs A)
 // After a scatter: the source buffer is empty, the queue cursor rewinds, and
 // the loop continues while the queue holds particles and the round cap is not
 // reached.  mode 0: after binning the parked records (start of a call);
-// mode 1: after binning a round's outgoing records.
-__global__ void ctrl_kernel(Ctrl *ctrl, uint32_t *src_count, int mode, cudaGraphConditionalHandle h, int use_graph)
+// mode 1: after binning a round's outgoing records.  With a brick window the
+// next round's part of the queue is the segments of the next window bricks
+// that hold particles (brick_cursor[b] is the end of brick b's segment once
+// the scatter is done); the others are carried (carry_kernel).
+__global__ void ctrl_kernel(Ctrl *ctrl, uint32_t *src_count, int mode, cudaGraphConditionalHandle h, int use_graph,
+                            const uint32_t *brick_cursor, int nb)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     *src_count = 0;
     ctrl->q_head = 0;
     if (mode == 1) ctrl->round += 1;
-    const bool more = ctrl->q_count > 0;
+    const uint32_t total = ctrl->q_count;
+    ctrl->q_total = total;
+    ctrl->win_start = 0;
+    const uint32_t w = ctrl->window;
+    if (w > 0 && total > 0 && (uint32_t)nb > w) {
+        uint32_t lo = ctrl->win_lo < (uint32_t)nb ? ctrl->win_lo : 0u;
+        uint32_t start = 0, end = 0;
+        for (int tries = 0; tries <= nb; ++tries) {        // a non-empty window exists: total > 0
+            const uint32_t hi = min(lo + w, (uint32_t)nb);
+            start = lo == 0 ? 0u : brick_cursor[lo - 1];
+            end = brick_cursor[hi - 1];
+            lo = hi >= (uint32_t)nb ? 0u : hi;
+            if (end > start) break;
+        }
+        ctrl->win_lo = lo;
+        ctrl->win_start = start;
+        ctrl->q_head = start;
+        ctrl->q_count = end;
+    }
+    const bool more = total > 0;
     const bool capped = ctrl->round >= ctrl->max_rounds;
     if (more && capped) ctrl->err |= CTRL_ERR_ROUND_LIMIT;
     if (!more || capped) ctrl->last_rounds = ctrl->round;
     if (use_graph) cudaGraphSetConditional(h, (more && !capped) ? 1u : 0u);
+}
+
+// After a round that advanced one brick window: the queue's records outside
+// the window, [0, win_start) and [q_count, q_total), join the round's
+// outgoing records, to be binned with them for the next round; then the
+// outgoing count takes them in (carry_fix_kernel, one thread, after every
+// copy is done).
+__global__ void carry_kernel(const Ctrl *ctrl, const Particle *q, Particle *o)
+{
+    if (ctrl->window == 0) return;
+    const uint32_t s = ctrl->win_start, e = ctrl->q_count, tot = ctrl->q_total, base = ctrl->o_count;
+    const uint32_t n = s + (tot - e);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t src = i < s ? i : e + (i - s);
+        const int4 *a = reinterpret_cast<const int4 *>(q + src);
+        int4 *d = reinterpret_cast<int4 *>(o + base + i);
+        d[0] = a[0];
+        d[1] = a[1];
+    }
+}
+
+__global__ void carry_fix_kernel(Ctrl *ctrl)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0 || ctrl->window == 0) return;
+    ctrl->o_count += ctrl->win_start + (ctrl->q_total - ctrl->q_count);
+}
+
+sg_status launch_carry(sg_tracer *t, cudaStream_t s)
+{
+    carry_kernel<<<t->ctx->sm_count * 2, 256, 0, s>>>(t->ctrl, t->q, t->o);
+    SG_CUDA(cudaGetLastError());
+    carry_fix_kernel<<<1, 32, 0, s>>>(t->ctrl);
+    SG_CUDA(cudaGetLastError());
+    return SG_OK;
 }
 
 // After the round loop of a call: if the round cap stopped it with particles
@@ -145,7 +202,7 @@ __global__ void __launch_bounds__(1024) park_rest_kernel(Ctrl *ctrl, const Parti
                                                          uint32_t *line_len)
 {
     if (!(ctrl->err & CTRL_ERR_ROUND_LIMIT)) return;
-    const uint32_t n = ctrl->q_count, base = ctrl->p_count;
+    const uint32_t n = ctrl->q_total, base = ctrl->p_count;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
         const int4 *s = reinterpret_cast<const int4 *>(q + i);
         const int4 r0 = s[0], r1 = s[1];
@@ -158,6 +215,7 @@ __global__ void __launch_bounds__(1024) park_rest_kernel(Ctrl *ctrl, const Parti
     if (threadIdx.x == 0) {
         ctrl->p_count = base + n;
         ctrl->q_count = 0;
+        ctrl->q_total = 0;
     }
 }
 
@@ -168,9 +226,13 @@ sg_status launch_park_rest(sg_tracer *t, cudaStream_t s)
     return SG_OK;
 }
 
-__global__ void prepare_kernel(Ctrl *ctrl, uint32_t horizon, uint32_t max_rounds)
+__global__ void prepare_kernel(Ctrl *ctrl, uint32_t horizon, uint32_t max_rounds, uint32_t window)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    ctrl->window = window;
+    ctrl->win_lo = 0;
+    ctrl->win_start = 0;
+    ctrl->q_total = 0;
     ctrl->q_count = 0;
     ctrl->q_head = 0;
     ctrl->o_count = 0;
@@ -182,7 +244,12 @@ __global__ void prepare_kernel(Ctrl *ctrl, uint32_t horizon, uint32_t max_rounds
 
 sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s)
 {
-    prepare_kernel<<<1, 32, 0, s>>>(t->ctrl, horizon, max_rounds);
+    // brick windows for the persistent kernels (they pop from the window's
+    // start); the one-launch-per-step kernel and partitioned tracers take
+    // every brick each round
+    const bool windowed = t->pod_world == 0 &&
+                          (t->p.kernel == SG_KERNEL_PERSISTENT || t->p.kernel == SG_KERNEL_LOCKSTEP);
+    prepare_kernel<<<1, 32, 0, s>>>(t->ctrl, horizon, max_rounds, windowed ? (uint32_t)t->p.brick_window : 0u);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }
@@ -198,7 +265,8 @@ sg_status launch_bin_args(const BinArgs &A, int sm_count, cudaStream_t s, bool i
     SG_CUDA(cudaGetLastError());
     bin_scatter_kernel<<<grid, 512, 0, s>>>(A);
     SG_CUDA(cudaGetLastError());
-    ctrl_kernel<<<1, 32, 0, s>>>(A.ctrl, A.src_count, mode, (cudaGraphConditionalHandle)cond_handle, in_graph ? 1 : 0);
+    ctrl_kernel<<<1, 32, 0, s>>>(A.ctrl, A.src_count, mode, (cudaGraphConditionalHandle)cond_handle, in_graph ? 1 : 0,
+                                 A.brick_cursor, A.n_local);
     SG_CUDA(cudaGetLastError());
     return SG_OK;
 }

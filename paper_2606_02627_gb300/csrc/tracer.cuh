@@ -194,6 +194,7 @@ sg_status launch_round(sg_tracer *t, cudaStream_t s);
 sg_status prepare_round(sg_tracer *t);
 sg_status launch_prepare_call(sg_tracer *t, uint32_t horizon, uint32_t max_rounds, cudaStream_t s);
 sg_status launch_park_rest(sg_tracer *t, cudaStream_t s);
+sg_status launch_carry(sg_tracer *t, cudaStream_t s);
 sg_status launch_iota(int32_t *dst, int64_t n, int64_t period, cudaStream_t s);
 sg_status launch_fill_inf(float *dst, long long n, cudaStream_t s);
 sg_status launch_set_q_count(Ctrl *ctrl, uint32_t n, cudaStream_t s);

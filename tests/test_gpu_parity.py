@@ -363,6 +363,46 @@ def test_round_cap_stops_with_consistent_partial_lines(ctx, turb64, layout, time
     assert torch.equal(final.status, whole.status)
 
 
+@pytest.mark.parametrize("layout,kernel,timed", [("cell8", "persistent", False), ("linear", "persistent", False),
+                                                 ("cell8", "lockstep", False), ("cell8", "persistent", True)])
+def test_brick_windows_give_the_same_bits(ctx, turb64, layout, kernel, timed):
+    # the brick-major rounds policy advances the particles of a few bricks per
+    # round and carries the others: the same arithmetic per particle, so the
+    # same lines as advancing every brick each round
+    from paper_2606_02627_gb300 import api
+    g, F, seeds, dt, _ = turb64
+    fld = make_field(ctx, g, F, bricks=(4, 4, 4), layout=layout)
+    _, base = run(ctx, fld, seeds, dt, 400, kernel=kernel, steps_per_round=37)
+    for w in (1, 5, 63):
+        tr = api.Tracer(ctx, fld, capacity=len(seeds), dt=dt, max_steps=400, kernel=kernel, steps_per_round=37,
+                        brick_window=w)
+        tr.upload_seeds(torch.from_numpy(seeds).cuda())
+        if timed:
+            ms, launches = tr.trace_timed()
+        else:
+            tr.trace()
+            tr.check()
+        lines = tr.get_lines()
+        torch.cuda.synchronize()
+        assert torch.equal(lines.offsets, base.offsets)
+        assert torch.equal(lines.vertices, base.vertices)
+        assert torch.equal(lines.status, base.status)
+
+
+def test_oversized_blocks_are_refused_at_creation(ctx):
+    # the kernels are built for at most 256 threads per CTA: a larger block is
+    # an argument error when the tracer (or batch) is made, not a failed launch
+    from paper_2606_02627_gb300 import _lib, api
+    g = inputs.cube_grid(9)
+    fld = make_field(ctx, g, inputs.uniform_field(g, (0.25, 0.0, 0.0)), layout="cell8")
+    with pytest.raises(_lib.StreamGBError) as ei:
+        api.Tracer(ctx, fld, capacity=16, dt=0.1, max_steps=10, block_size=512)
+    assert ei.value.code == _lib.SG_ERR_INVALID_ARG
+    with pytest.raises(_lib.StreamGBError) as ei:
+        api.Batch(ctx, max_lines=64, slab_bytes=1 << 20, block_size=512)
+    assert ei.value.code == _lib.SG_ERR_INVALID_ARG
+
+
 def test_step_reports_active_lines(ctx):
     from paper_2606_02627_gb300 import api
     g = inputs.cube_grid(16)
