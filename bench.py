@@ -69,7 +69,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU work of the oracle baseline")
     ap.add_argument("--schedule", default="", help="block,blocks_per_sm,steps_per_round[,drain_steps]")
     ap.add_argument("--requests", type=int, default=160, help="serve: requests in the Poisson stream")
-    ap.add_argument("--config", default="steady", choices=["steady", "streak", "serve", "umesh"],
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end pass through host buffers (large workloads whose CSR would not fit a "
+                         "page-locked host buffer)")
+    ap.add_argument("--config", default="steady", choices=["steady", "streak", "serve", "umesh", "plain"],
                     help="steady: brick-decomposed streamlines (the headline); streak: unsteady streaklines with "
                          "time slices streamed from page-locked host memory")
     ap.add_argument("--host-loop", action="store_true",
@@ -476,9 +479,70 @@ def run_serve(args, rank, world, local):
     print(json.dumps(out))
 
 
+def run_plain(args, rank, world, local):
+    """The plain method on one brick: a 64^3 FP32 field of solid-body rotation and of ABC flow on [0, 2pi]^3,
+    1024 seeds uniform in the interior (seed 0), RK4 with h = 0.25 cell, max 500 steps, stop on exit or
+    |v| < 1e-6; the persistent kernel on CELL8 records and the plain per-seed kernel on the float3 array.
+    One step = seed upload + trace + CSR compaction (the field stays resident).  Latency-bound: 1024 lines
+    on 152 SMs."""
+    import torch
+    from paper_2606_02627_gb300 import api, inputs
+    from paper_2606_02627_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    ctx = api.Context(local)
+    g = inputs.cube_grid(64)
+    seeds = torch.from_numpy(inputs.uniform_seeds(g, 1024, 0, lo_cells=1.0)).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    for which in ("rotation", "abc"):
+        F = inputs.rotation_field(g) if which == "rotation" else inputs.abc_field(g)
+        Fd = torch.from_numpy(F).to(dev)
+        sp = torch.tensor(g.spacing, device=dev, dtype=torch.float32)
+        dt = 0.25 / float((Fd / sp).norm(dim=-1).max())
+        for kernel, layout in (("persistent", "cell8"), ("per_seed", "global")):
+            fld = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(1, 1, 1), dtype="f32", layout=layout)
+            fld.set_global(Fd, stream=stream)
+            tr = api.Tracer(ctx, fld, capacity=1024, dt=dt, max_steps=500, kernel=kernel)
+            nl = tr.capacity
+            off = torch.empty(nl + 1, dtype=torch.int64, device=dev)
+            vert = torch.empty((nl * 501, 3), dtype=torch.float32, device=dev)
+
+            def one():
+                tr.upload_seeds(seeds, stream=stream)
+                tr.trace(stream=stream)
+                api.call("sg_tracer_get_lines", tr.h, None, None, api._ptr(off), api._ptr(vert), None, None, None,
+                         api._stream(stream))
+            for _ in range(args.warmup):
+                one()
+            stream.synchronize()
+            steps = tr.total_steps(stream=stream)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                one()
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            res[f"{which}_{kernel}"] = {"value": steps / (ms / 1e3), "ms_per_step": ms, "particle_steps": steps}
+            del tr, fld
+    out = {"metric": "RK4 particle-steps/s (plain method, one brick)", "value": res["abc_persistent"]["value"],
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": res["abc_persistent"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "plain method: 64^3 FP32 rotation / ABC flow on [0,2pi]^3, 1 brick, 1024 seeds "
+                                  "(seed 0), RK4 h=0.25 cell, max 500 steps"},
+           "variants": res}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.config == "plain":
+        return run_plain(args, rank, world, local)
     if args.config in ("streak", "umesh") and args.dtype != "f32":
         raise SystemExit(f"--config {args.config} stores its field in FP32 only (--dtype f32)")
     if args.config == "streak":
@@ -558,7 +622,7 @@ def main():
 
     seeds_np = inputs.uniform_seeds(grid, args.seeds, rank_seed(1, rank))
     seeds_dev = torch.from_numpy(seeds_np).to(dev)
-    seeds_pin = torch.from_numpy(seeds_np).pin_memory()
+    seeds_pin = torch.from_numpy(seeds_np).pin_memory() if not args.no_e2e else None
 
     def make(dtype, layout, kernel, bricks=(4, 4, 4), extra=None):
         fld = api.Field(ctx, grid.dims, grid.origin, grid.spacing,
@@ -714,13 +778,15 @@ def main():
 
     # e2e through the C ABI: seeds from pinned host, CSR lines to pinned host (copy overlapping the next
     # step), inside the timed region
-    ems, _, etot_all, d2h = timed(fld, tr, 2, max(1, args.steps), seeds_pin, host_out=True)
-    e2e = {"value": etot_all / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(seeds_pin.numel() * 4),
-           "d2h_bytes_per_step": int(d2h), "ms_per_step": ems}
-    # the host link it runs on: one 2 GiB page-locked copy each way (the step's D2H copy overlaps the next
-    # step's trace, so the step takes about max(trace, D2H copy) plus the pipeline's fill and drain)
-    e2e.update(copy_rates(dev))
-    e2e["d2h_ms_per_step"] = d2h / (e2e["d2h_gbs"] * 1e9) * 1e3
+    e2e = None
+    if not args.no_e2e:
+        ems, _, etot_all, d2h = timed(fld, tr, 2, max(1, args.steps), seeds_pin, host_out=True)
+        e2e = {"value": etot_all / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(seeds_pin.numel() * 4),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": ems}
+        # the host link it runs on: one 2 GiB page-locked copy each way (the step's D2H copy overlaps the next
+        # step's trace, so the step takes about max(trace, D2H copy) plus the pipeline's fill and drain)
+        e2e.update(copy_rates(dev))
+        e2e["d2h_ms_per_step"] = d2h / (e2e["d2h_gbs"] * 1e9) * 1e3
     del tr, fld
     torch.cuda.empty_cache()
 
