@@ -640,8 +640,8 @@ sg_status sg_lines_compact(const float *slab, int64_t max_vertices_per_line, con
  * the library's copy of the array with the context) the call must not be used
  * on it again in the same process.  All calls on a device share the
  * one scratch array and it keeps the last call's contents: calls that overlap
- * on the GPU (different streams, or graphs launched concurrently) race and
- * must be ordered by the caller.  Asynchronous on `stream`. */
+ * on the GPU (issued on different streams) race and must be ordered by the
+ * caller.  Asynchronous on `stream`. */
 sg_status sg_lines_compact_static(const float *slab, int64_t max_vertices_per_line, const uint32_t *lengths,
                                   int64_t n_lines, int64_t *offsets, float *vertices, void *stream);
 
