@@ -366,14 +366,18 @@ sg_status sg_tracer_get_lines(sg_tracer *t, int64_t *n_lines, int64_t *n_vertice
  * tracer buffer) overlaps it.  The call synchronises `stream` (the sizes are
  * read), gathers the CSR into device staging memory owned by the tracer
  * (grown on demand, freed by sg_tracer_destroy) on `stream`, and returns
- * without waiting for the copy.  n_lines / n_vertices (host, nullable)
+ * without waiting for the copy.  The tracer keeps two staging buffers of
+ * the CSR's size and uses them in turn, so that the gather of one readout
+ * does not wait for the copy of the one before (if the second cannot be
+ * allocated, the first serves every readout).  n_lines / n_vertices (host, nullable)
  * receive the sizes; with every buffer NULL the call stops there.  Buffers
  * (each nullable, page-locked host memory, else SG_ERR_INVALID_ARG): n_lines+1
  * int64 offsets, 3*n_vertices floats, n_lines status bytes, n_lines float
  * margins, as in sg_tracer_get_lines.  They are complete once a stream made
  * to wait by sg_tracer_wait_lines has reached that point; a later overlapped
- * readout waits (on `stream`) for the previous copy before reusing the
- * staging memory.  SG_ERR_STATE for streakline tracers. */
+ * readout waits (on `stream`) for the copy of the readout that last used the
+ * same staging buffer before reusing it.  SG_ERR_STATE for streakline
+ * tracers. */
 sg_status sg_tracer_get_lines_overlapped(sg_tracer *t, int64_t *n_lines, int64_t *n_vertices, int64_t *offsets,
                                          float *vertices, uint8_t *status, float *margin, void *stream);
 

@@ -344,8 +344,10 @@ extern "C" sg_status sg_tracer_create(sg_context *ctx, sg_field *f, const sg_tra
             if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t->ev_copied[k], cudaEventDisableTiming);
         }
         if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t->ev_ovl_gathered, cudaEventDisableTiming);
-        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&t->ev_ovl_copied, cudaEventDisableTiming);
-        if (ce == cudaSuccess) ce = cudaEventRecord(t->ev_ovl_copied, t->copy_stream);
+        for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
+            ce = cudaEventCreateWithFlags(&t->ev_ovl_copied[k], cudaEventDisableTiming);
+            if (ce == cudaSuccess) ce = cudaEventRecord(t->ev_ovl_copied[k], t->copy_stream);
+        }
         if (ce != cudaSuccess) {
             sg_tracer_destroy(t);
             return cuda_error(ce, "readback stream");
@@ -372,12 +374,14 @@ extern "C" sg_status sg_tracer_destroy(sg_tracer *t)
         if (t->ev_gathered[k]) cudaEventDestroy(t->ev_gathered[k]);
         if (t->ev_copied[k]) cudaEventDestroy(t->ev_copied[k]);
     }
-    if (t->ovl_buf) {
-        if (t->ev_ovl_copied) cudaEventSynchronize(t->ev_ovl_copied);
-        cudaFree(t->ovl_buf);
+    for (int k = 0; k < 2; ++k) {
+        if (t->ovl_buf[k]) {
+            if (t->ev_ovl_copied[k]) cudaEventSynchronize(t->ev_ovl_copied[k]);
+            cudaFree(t->ovl_buf[k]);
+        }
+        if (t->ev_ovl_copied[k]) cudaEventDestroy(t->ev_ovl_copied[k]);
     }
     if (t->ev_ovl_gathered) cudaEventDestroy(t->ev_ovl_gathered);
-    if (t->ev_ovl_copied) cudaEventDestroy(t->ev_ovl_copied);
     if (t->copy_stream) cudaStreamDestroy(t->copy_stream);
     delete t;
     return SG_OK;
@@ -788,19 +792,41 @@ extern "C" sg_status sg_tracer_get_lines_overlapped(sg_tracer *t, int64_t *n_lin
     const size_t o_st = o_vert + align_up(sizeof(float) * 3 * nv, 256);
     const size_t o_mg = o_st + align_up(nl, 256);
     const size_t need = o_mg + align_up(sizeof(float) * nl, 256);
-    if (need > t->ovl_bytes) {
-        // the previous copy still reads the old buffer
-        SG_CUDA(cudaEventSynchronize(t->ev_ovl_copied));
-        if (t->ovl_buf) SG_CUDA(cudaFree(t->ovl_buf));
-        t->ovl_buf = nullptr;
-        t->ovl_bytes = 0;
-        const size_t bytes = align_up(need, (size_t)2 << 20);
-        SG_CUDA(cudaMalloc(&t->ovl_buf, bytes));
-        t->ovl_bytes = bytes;
+    const size_t bytes = align_up(need, (size_t)2 << 20);
+    // this readout's staging buffer: the two alternate; if the second cannot
+    // be allocated, the first serves every readout
+    int k = t->ovl_single ? 0 : t->ovl_next;
+    if (need > t->ovl_bytes[k]) {
+        // the copy of the readout that used this buffer still reads it
+        SG_CUDA(cudaEventSynchronize(t->ev_ovl_copied[k]));
+        if (t->ovl_buf[k]) SG_CUDA(cudaFree(t->ovl_buf[k]));
+        t->ovl_buf[k] = nullptr;
+        t->ovl_bytes[k] = 0;
+        cudaError_t ae = cudaMalloc(&t->ovl_buf[k], bytes);
+        if (ae == cudaErrorMemoryAllocation && k == 1) {
+            (void)cudaGetLastError();            // not sticky: the first buffer serves from now on
+            t->ovl_buf[k] = nullptr;
+            t->ovl_single = true;
+            k = 0;
+            if (need > t->ovl_bytes[0]) {
+                SG_CUDA(cudaEventSynchronize(t->ev_ovl_copied[0]));
+                if (t->ovl_buf[0]) SG_CUDA(cudaFree(t->ovl_buf[0]));
+                t->ovl_buf[0] = nullptr;
+                t->ovl_bytes[0] = 0;
+                SG_CUDA(cudaMalloc(&t->ovl_buf[0], bytes));
+                t->ovl_bytes[0] = bytes;
+            }
+        } else {
+            SG_CUDA(ae);
+            t->ovl_bytes[k] = bytes;
+        }
     }
-    char *b = t->ovl_buf;
-    // the gather overwrites the staging memory only after the previous copy read it
-    SG_CUDA(cudaStreamWaitEvent(s, t->ev_ovl_copied, 0));
+    t->ovl_next = k ^ 1;
+    t->ovl_last = k;
+    char *b = t->ovl_buf[k];
+    // the gather overwrites the staging memory only after the copy of the
+    // readout that used it last has read it
+    SG_CUDA(cudaStreamWaitEvent(s, t->ev_ovl_copied[k], 0));
     st = launch_gather_lines(t, (int64_t *)(b + o_off), (float *)(b + o_vert), (uint8_t *)(b + o_st),
                              (float *)(b + o_mg), s);
     if (st) return st;
@@ -814,7 +840,7 @@ extern "C" sg_status sg_tracer_get_lines_overlapped(sg_tracer *t, int64_t *n_lin
     if (status && nl) SG_CUDA(cudaMemcpyAsync(status, b + o_st, nl, cudaMemcpyDeviceToHost, t->copy_stream));
     if (margin && nl)
         SG_CUDA(cudaMemcpyAsync(margin, b + o_mg, sizeof(float) * nl, cudaMemcpyDeviceToHost, t->copy_stream));
-    SG_CUDA(cudaEventRecord(t->ev_ovl_copied, t->copy_stream));
+    SG_CUDA(cudaEventRecord(t->ev_ovl_copied[k], t->copy_stream));
     return SG_OK;
 }
 
@@ -823,7 +849,8 @@ extern "C" sg_status sg_tracer_wait_lines(sg_tracer *t, void *stream)
     SG_CHECK(t != nullptr, SG_ERR_INVALID_ARG, "tracer is NULL");
     SG_CHECK(t->p.mode != SG_STREAKLINE, SG_ERR_STATE, "overlapped readout is for streamline and path-line tracers");
     SG_CUDA(cudaSetDevice(t->ctx->device));
-    SG_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, t->ev_ovl_copied, 0));
+    // the copies run in order on the copy stream: the last one covers them all
+    SG_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, t->ev_ovl_copied[t->ovl_last], 0));
     return SG_OK;
 }
 

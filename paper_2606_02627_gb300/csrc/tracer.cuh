@@ -134,11 +134,16 @@ struct sg_tracer {
     cudaEvent_t ev_gathered[2];
     cudaEvent_t ev_copied[2];
     // overlapped readout: the whole CSR gathered into device memory, then
-    // copied to the host on copy_stream while the caller's stream moves on
-    char *ovl_buf;               // device, grown on demand
-    size_t ovl_bytes;
+    // copied to the host on copy_stream while the caller's stream moves on;
+    // two staging buffers used in turn (the second only once it could be
+    // allocated), so a readout waits for the copy of the one two back
+    char *ovl_buf[2];            // device, grown on demand
+    size_t ovl_bytes[2];
     cudaEvent_t ev_ovl_gathered;
-    cudaEvent_t ev_ovl_copied;
+    cudaEvent_t ev_ovl_copied[2];
+    int ovl_next;                // staging buffer of the next readout
+    int ovl_last;                // staging buffer of the last readout
+    bool ovl_single;             // the second buffer could not be allocated
     // streaklines
     int64_t n_release;
     int32_t births;              // births released so far

@@ -5,6 +5,10 @@
   2048 sampled lines against the FP64 oracle on the FP32 field, plus
   properties that hold for every line (status set, lengths within the cap,
   vertices inside the domain, total steps = sum of lengths - 1).
+* The same 512^3 FP32 workload under the schedules the autotuner picks for
+  the benchmark's headline (256 x 4 CTAs per SM and 512 steps per round; 128
+  x 6 and 128 steps with no drain limit): the same lines, bit for bit, as the
+  default schedule (whose lines are checked against the oracle above).
 * 1024^3 turbulence (seed 2), 4M seeds, max 1000 steps, FP32 / FX21 / BF16 /
   FP16 storage: vertex error on the first 10k seeds against the FP64 oracle on
   the FP32 field (max and p99 reported; the 1e-3 FP32 bound and the 5e-2
@@ -48,11 +52,11 @@ class Sub:
         self.margin = lines.margin[ii].cpu()
 
 
-def trace_full(ctx, g, F, seeds, dt, max_steps, dtype, layout="cell8"):
+def trace_full(ctx, g, F, seeds, dt, max_steps, dtype, layout="cell8", **sched):
     from paper_2606_02627_gb300 import api
     fld = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(4, 4, 4), dtype=dtype, layout=layout)
     fld.set_global(F)
-    tr = api.Tracer(ctx, fld, capacity=seeds.shape[0], dt=dt, max_steps=max_steps)
+    tr = api.Tracer(ctx, fld, capacity=seeds.shape[0], dt=dt, max_steps=max_steps, **sched)
     tr.upload_seeds(seeds)
     tr.trace()
     tr.check()
@@ -107,6 +111,27 @@ def test_512_bench_configuration_sampled_lines(ctx):
                         for i in range(len(idx)) for k in [min(off[i + 1] - off[i], ref.length[i], 1001)] if k)
             print(f"512^3 f32: max err over the first 1000 steps {e1000:.2e}")
             assert e1000 <= 1e-3
+
+
+def test_512_tuned_schedules_same_bits(ctx):
+    g = inputs.cube_grid(512)
+    F = inputs.turbulence_field(g, inputs.turbulence_modes(1), device="cuda")
+    seeds = torch.from_numpy(inputs.uniform_seeds(g, 1 << 20, 1)).cuda()
+    from paper_2606_02627_gb300 import api
+    probe = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(4, 4, 4))
+    probe.set_global(F)
+    dt = 0.5 / probe.max_speed()
+    probe.close()
+    base, steps = trace_full(ctx, g, F, seeds, dt, 2000, "f32")
+    for sched in (dict(block_size=256, blocks_per_sm=4, steps_per_round=512),
+                  dict(block_size=128, blocks_per_sm=6, steps_per_round=128, drain_steps=-1)):
+        lines, st = trace_full(ctx, g, F, seeds, dt, 2000, "f32", **sched)
+        assert st == steps
+        assert torch.equal(lines.offsets, base.offsets)
+        assert torch.equal(lines.status, base.status)
+        assert torch.equal(lines.vertices, base.vertices), sched
+        del lines
+        torch.cuda.empty_cache()
 
 
 def test_1024_precision_forms_error_on_10k_seeds(ctx):
