@@ -249,18 +249,30 @@ def reduce_over_ranks(ms: float, steps: int, dist, device):
     return float(t.item()), int(s.item())
 
 
-def cpu_oracle_rate(F_host, grid, seeds, dt, max_steps, seconds, nthreads=None):
+def cpu_oracle_rate(F_host, grid, seeds, dt, max_steps, seconds, nthreads=None, n_seeds=None):
     """Oracle particle-steps/s on the host cores (all of them unless nthreads is given) over a bounded
-    prefix of the seeds."""
+    prefix of the seeds: sized to take about `seconds`, or the first n_seeds when given."""
     import oracle
     nthreads = nthreads or oracle.default_threads()
+    if n_seeds:
+        t = time.perf_counter()
+        L = oracle.trace_streamlines(F_host, grid.origin, grid.spacing, seeds[:n_seeds], dt, max_steps, eps=1e-6,
+                                     nthreads=nthreads)
+        t0 = time.perf_counter() - t
+        steps = int(L.steps().sum())
+        return steps / t0, nthreads, n_seeds, steps, t0
     n0 = min(len(seeds), max(nthreads * 8, 64))
     t = time.perf_counter()
     L = oracle.trace_streamlines(F_host, grid.origin, grid.spacing, seeds[:n0], dt, max_steps, eps=1e-6,
                                  nthreads=nthreads)
     t0 = time.perf_counter() - t
-    n = int(min(len(seeds), max(n0, n0 * seconds / max(t0, 1e-3))))
-    if n > n0:
+    n = n0
+    # a small calibration run overestimates the time per seed (start-up, load imbalance): rescale until
+    # the sample takes at least half the target, at most three times
+    for _ in range(3):
+        if t0 >= 0.5 * seconds or n >= len(seeds):
+            break
+        n = int(min(len(seeds), max(n + 1, n * seconds / max(t0, 1e-3))))
         t = time.perf_counter()
         L = oracle.trace_streamlines(F_host, grid.origin, grid.spacing, seeds[:n], dt, max_steps, eps=1e-6,
                                      nthreads=nthreads)
@@ -581,8 +593,9 @@ def main():
         rates = []
         info = None
         for it in range(args.warmup + args.steps):
+            # the first step sizes the prefix; every step traces the same seeds
             rate, cores, ns, steps, secs = cpu_oracle_rate(F_host, grid, seeds, dt, args.max_steps,
-                                                           args.cpu_seconds / 2)
+                                                           args.cpu_seconds / 2, n_seeds=info[1] if info else None)
             if it >= args.warmup:
                 rates.append(rate)
             info = (cores, ns, steps, secs)
