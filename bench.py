@@ -324,7 +324,10 @@ def run_umesh(args, rank, world, local):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": "unstructured: 128^3 grid cells of turbulence (seed 1) as 2,097,152 jittered "
                                   "hexahedra, BVH point location, 262144 seeds, RK4 h=0.5 cell, max 1000 steps",
-                      "cells": mesh.n_cells, "mesh_build_s": build_s},
+                      "cells": mesh.n_cells, "mesh_build_s": build_s,
+                      "mesh_device_bytes": int(mesh.workspace.numel()),
+                      "mesh_bytes_per_cell": round(mesh.workspace.numel() / max(1, mesh.n_cells), 1),
+                      "mean_steps_per_line": round(steps_total / seeds.shape[0], 1)},
            "particle_steps_per_step": steps_total}
     print(json.dumps(out))
 

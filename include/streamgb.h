@@ -474,8 +474,8 @@ sg_status sg_tracer_line_buffers(sg_tracer *t, float **slab, uint32_t **length, 
 typedef struct sg_umesh sg_umesh;
 enum { SG_CELL_TET = 4, SG_CELL_PYRAMID = 5, SG_CELL_PRISM = 6, SG_CELL_HEX = 8 };
 
-/* Workspace bytes of a mesh of n_cells cells (256 B per cell record, 64 B per
- * cell of hierarchy, 4 B of index). */
+/* Workspace bytes of a mesh of n_cells cells (256 B per cell record, 32 B per
+ * cell of hierarchy: at most one node per cell, 4 B of index). */
 sg_status sg_umesh_required_bytes(int64_t n_cells, size_t *bytes);
 
 /* vertices, velocity: host, n_vertices x 3 floats (world); cell_vertices,

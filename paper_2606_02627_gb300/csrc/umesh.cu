@@ -428,7 +428,10 @@ struct BuildItem {
     int node, first, count;
 };
 
-static int64_t max_nodes(int64_t n_cells) { return n_cells > 0 ? 2 * n_cells : 1; }
+// The median split turns a node of more than UMESH_LEAF (4) cells into two
+// of at least 2, so every leaf of a hierarchy over n >= 2 cells holds 2 to 4
+// cells: at most n / 2 leaves and n - 1 nodes.
+static int64_t max_nodes(int64_t n_cells) { return n_cells > 1 ? n_cells : 1; }
 
 }  // namespace sg
 
@@ -589,6 +592,8 @@ extern "C" sg_status sg_umesh_create(sg_context *ctx, const float *vertices, con
             memcpy(&sorted[(size_t)b].x[1 + q.slot].w, &a, 4);
         }
     }
+    SG_CHECK((int64_t)nodes.size() <= max_nodes(n_cells), SG_ERR_STATE, "hierarchy of %zu nodes exceeds its bound",
+             nodes.size());
     SG_CUDA(cudaSetDevice(ctx->device));
     Carve cv{(char *)workspace, 0, 0};
     UCell *dcells = (UCell *)cv.take(sizeof(UCell) * (size_t)n_cells);

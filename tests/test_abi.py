@@ -68,6 +68,19 @@ def test_field_size_query_and_validation(lib):
     assert L.sg_field_required_bytes(ctypes.byref(glob), ctypes.byref(n)) == lib.SG_ERR_INVALID_ARG
 
 
+def test_umesh_size_query(lib):
+    """A mesh's workspace: 256-B cell records, at most one 32-B hierarchy node
+    per cell (leaves of 2 to 4 cells), a 4-B index per cell, each part
+    256-byte aligned."""
+    L = lib.lib()
+    up = lambda x: (x + 255) // 256 * 256
+    n = ctypes.c_size_t()
+    for cells in (0, 1, 2, 5, 1000, 2_097_152):
+        assert L.sg_umesh_required_bytes(cells, ctypes.byref(n)) == 0
+        assert n.value == up(256 * cells) + up(32 * max(cells, 1)) + up(4 * cells), cells
+    assert L.sg_umesh_required_bytes(-1, ctypes.byref(n)) == lib.SG_ERR_INVALID_ARG
+
+
 def test_context_without_gpu_fails_cleanly(lib):
     import torch
     if torch.cuda.is_available():
