@@ -284,8 +284,9 @@ def cpu_oracle_rate(F_host, grid, seeds, dt, max_steps, seconds, nthreads=None, 
 def run_umesh(args, rank, world, local):
     """Unstructured field: the cells of a 128^3 grid of the synthetic turbulence (seed 1, 256 modes, |k| <= 16
     on [0, 2pi]^3) as 2,097,152 hexahedra with interior vertices jittered by up to 0.1 cell (the paper's
-    galaxy-as-hexahedra variant, synthetic); 262,144 seeds, RK4 h = 0.5 cell, max 1000 steps; one thread per
-    seed, cells located through the BVH.  Step = trace + CSR compaction (the mesh is built once)."""
+    galaxy-as-hexahedra variant, synthetic); 262,144 seeds, RK4 h = 0.5 cell, max 1000 steps, in rounds of at
+    most 128 steps per particle; cells located by face walks and the BVH.  Step = trace + CSR compaction (the
+    mesh is built once)."""
     import numpy as np
     import torch
     from paper_2606_02627_gb300 import api, inputs

@@ -494,10 +494,14 @@ sg_status sg_umesh_destroy(sg_umesh *m);
  * for none).  Asynchronous. */
 sg_status sg_umesh_sample(sg_umesh *m, const float *points, int64_t n, float *velocity, int64_t *cell, void *stream);
 
-/* Streamlines from n seeds (device, world): line i's vertices go to slab +
- * 3 i (max_steps + 1) (device), its vertex count to length[i], its status
- * (SG_LINE_*, tie bit for EXIT margins < 1e-3) and margin likewise (all
- * device).  Compact with sg_lines_compact.  Asynchronous. */
+/* Streamlines from n seeds (device, world; n < 2^31): line i's vertices go
+ * to slab + 3 i (max_steps + 1) (device), its vertex count to length[i], its
+ * status (SG_LINE_*, tie bit for EXIT margins < 1e-3) and margin likewise
+ * (all device).  The particles advance in rounds of at most 128 steps; with
+ * max_steps above 128 the call takes its two particle queues (128 B per
+ * seed) from the device's stream-ordered memory pool on `stream`
+ * (cudaMallocAsync) and returns them there.  Compact with sg_lines_compact.
+ * Asynchronous. */
 sg_status sg_umesh_trace(sg_umesh *m, const float *seeds, int64_t n, double dt, int32_t max_steps, float eps,
                          float *slab, uint32_t *length, uint8_t *status, float *margin, void *stream);
 

@@ -45,6 +45,7 @@ constexpr int UMESH_LEAF = 4;
 constexpr int UMESH_STACK = 64;
 constexpr int UMESH_NEWTON = 12;
 constexpr int UMESH_WALK = 6;                  // cells visited by a walk before the BVH takes over
+constexpr int UMESH_SEGMENT = 128;             // steps per particle per round of a trace
 
 // Faces of each cell type (VTK vertex order), in the order of the parametric
 // bounds that exit_face reports: hexahedron a<0, a>1, b<0, b>1, c<0, c>1;
@@ -383,27 +384,77 @@ __device__ int urk4(const UMeshView &M, double3 p, float dt, float eps, long lon
     return SG_LINE_ACTIVE;
 }
 
-__global__ void __launch_bounds__(256) umesh_trace_kernel(UMeshView M, UTraceArgs A)
+// A particle between rounds: its FP64 position, the cell found for it, its
+// coordinates and velocity there (what the next step starts from), its line
+// and its step count.
+struct UPart {
+    double p[3];
+    float r[3];
+    float v[3];
+    int32_t hint;
+    uint32_t line;
+    uint32_t step;
+    uint32_t pad;
+};
+static_assert(sizeof(UPart) == 64, "UPart");
+
+// One round of the unstructured trace: every particle of the round's queue
+// (round 0: the seeds, located here) takes at most `seg` steps; a particle
+// that neither stopped nor reached max_steps goes to the next round's queue.
+// Lines end at different lengths, so a launch that traced every line to its
+// end would run as long as the longest line of each warp; rounds of a bounded
+// number of steps keep the lanes of a warp busy until the last round.  A
+// particle's state carries over whole, so its steps are the same as in one
+// uninterrupted loop.
+struct URound {
+    const UPart *in;             // nullptr: the seeds
+    const uint32_t *in_count;
+    UPart *out;
+    uint32_t *out_count;
+    uint32_t seg;
+};
+
+__global__ void __launch_bounds__(256) umesh_round_kernel(UMeshView M, UTraceArgs A, URound R)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += (long long)gridDim.x * blockDim.x) {
-        double3 p = make_double3(A.seeds[3 * i], A.seeds[3 * i + 1], A.seeds[3 * i + 2]);
+    const long long n = R.in ? (long long)*R.in_count : A.n;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double3 p;
+        long long hint;
         float r[3];
-        long long hint = ulocate(M, p, -1, r);
-        float margin = INFINITY;
-        A.margin[i] = INFINITY;
-        if (hint < 0) {
-            A.len[i] = 0;
-            A.status[i] = SG_LINE_OUT;
-            continue;
+        float3 v0;
+        uint32_t line, step;
+        if (!R.in) {
+            line = (uint32_t)i;
+            step = 0;
+            p = make_double3(A.seeds[3 * i], A.seeds[3 * i + 1], A.seeds[3 * i + 2]);
+            hint = ulocate(M, p, -1, r);
+            A.margin[i] = INFINITY;
+            if (hint < 0) {
+                A.len[i] = 0;
+                A.status[i] = SG_LINE_OUT;
+                continue;
+            }
+            float *o = A.slab + i * A.W * 3;
+            o[0] = A.seeds[3 * i];
+            o[1] = A.seeds[3 * i + 1];
+            o[2] = A.seeds[3 * i + 2];
+            v0 = ucell_value(M.cells[hint], r);
+        } else {
+            const UPart &q = R.in[i];
+            p = make_double3(q.p[0], q.p[1], q.p[2]);
+            hint = q.hint;
+            r[0] = q.r[0];
+            r[1] = q.r[1];
+            r[2] = q.r[2];
+            v0 = make_float3(q.v[0], q.v[1], q.v[2]);
+            line = q.line;
+            step = q.step;
         }
-        float *out = A.slab + i * A.W * 3;
-        out[0] = A.seeds[3 * i];
-        out[1] = A.seeds[3 * i + 1];
-        out[2] = A.seeds[3 * i + 2];
-        float3 v0 = ucell_value(M.cells[hint], r);
-        uint32_t step = 0;
-        int st = SG_LINE_MAXSTEPS;
-        while (step < A.max_steps) {
+        float *out = A.slab + (long long)line * A.W * 3;
+        float margin = INFINITY;
+        int st = SG_LINE_ACTIVE;
+        const uint32_t stop = step + min(R.seg, A.max_steps - step);
+        while (step < stop) {
             double3 pn;
             const int s = urk4(M, p, A.dt, A.eps, hint, r, v0, pn, margin);
             if (s != SG_LINE_ACTIVE) {
@@ -416,9 +467,34 @@ __global__ void __launch_bounds__(256) umesh_trace_kernel(UMeshView M, UTraceArg
             st_na(out + 3ll * step + 1, (float)p.y);
             st_na(out + 3ll * step + 2, (float)p.z);
         }
-        A.len[i] = step + 1;
-        A.status[i] = stop_code_t(st, margin, A.tie_cells, A.tie_eps_rel);
-        A.margin[i] = margin;
+        if (st == SG_LINE_ACTIVE && step >= A.max_steps) st = SG_LINE_MAXSTEPS;
+        if (st != SG_LINE_ACTIVE) {
+            A.len[line] = step + 1;
+            A.status[line] = stop_code_t(st, margin, A.tie_cells, A.tie_eps_rel);
+            A.margin[line] = margin;
+        } else {
+            // warp-aggregated append to the next round's queue
+            const unsigned m = __activemask();
+            const int leader = __ffs(m) - 1;
+            const unsigned lane = threadIdx.x & 31u;
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(R.out_count, (uint32_t)__popc(m));
+            base = __shfl_sync(m, base, leader);
+            UPart &q = R.out[base + __popc(m & ((1u << lane) - 1u))];
+            q.p[0] = p.x;
+            q.p[1] = p.y;
+            q.p[2] = p.z;
+            q.r[0] = r[0];
+            q.r[1] = r[1];
+            q.r[2] = r[2];
+            q.v[0] = v0.x;
+            q.v[1] = v0.y;
+            q.v[2] = v0.z;
+            q.hint = (int32_t)hint;
+            q.line = line;
+            q.step = step;
+            q.pad = 0u;
+        }
     }
 }
 
@@ -655,7 +731,8 @@ extern "C" sg_status sg_umesh_sample(sg_umesh *m, const float *points, int64_t n
 extern "C" sg_status sg_umesh_trace(sg_umesh *m, const float *seeds, int64_t n, double dt, int32_t max_steps, float eps,
                                     float *slab, uint32_t *length, uint8_t *status, float *margin, void *stream)
 {
-    SG_CHECK(m && n >= 0 && max_steps >= 0 && max_steps < (1 << 27), SG_ERR_INVALID_ARG, "bad arguments");
+    SG_CHECK(m && n >= 0 && n <= 0x7fffffff && max_steps >= 0 && max_steps < (1 << 27), SG_ERR_INVALID_ARG,
+             "bad arguments");
     SG_CHECK(dt > 0.0 && dt < 1e30 && eps >= 0.f, SG_ERR_INVALID_ARG, "bad dt or eps");
     if (n == 0) return SG_OK;
     for (const void *p : {(const void *)seeds, (const void *)slab, (const void *)length, (const void *)status,
@@ -678,7 +755,34 @@ extern "C" sg_status sg_umesh_trace(sg_umesh *m, const float *seeds, int64_t n, 
     long long g = (n + 255) / 256;
     const long long cap = (long long)m->ctx->sm_count * 8;
     if (g > cap) g = cap;
-    umesh_trace_kernel<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(view_of(m), A);
-    SG_CUDA(cudaGetLastError());
+    // rounds of at most UMESH_SEGMENT steps per particle; after
+    // ceil(max_steps / UMESH_SEGMENT) of them (at least one) every line has
+    // ended, so the queue lengths stay on the device
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rounds = max_steps > 0 ? (max_steps + UMESH_SEGMENT - 1) / UMESH_SEGMENT : 1;
+    const size_t qbytes = align_up(sizeof(UPart) * (size_t)n, 256);
+    char *buf = nullptr;
+    if (rounds > 1) SG_CUDA(cudaMallocAsync((void **)&buf, 2 * qbytes + 256, s));
+    UPart *q[2] = {buf ? (UPart *)buf : nullptr, buf ? (UPart *)(buf + qbytes) : nullptr};
+    uint32_t *cnt = buf ? (uint32_t *)(buf + 2 * qbytes) : nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < rounds && e == cudaSuccess; ++r) {
+        URound R;
+        R.in = r == 0 ? nullptr : q[(r - 1) & 1];
+        R.in_count = r == 0 ? nullptr : cnt + ((r - 1) & 1);
+        R.out = q[r & 1];
+        R.out_count = cnt ? cnt + (r & 1) : nullptr;
+        R.seg = rounds > 1 ? (uint32_t)UMESH_SEGMENT : (uint32_t)max_steps;
+        if (R.out_count) e = cudaMemsetAsync(R.out_count, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) {
+            umesh_round_kernel<<<(unsigned)g, 256, 0, s>>>(view_of(m), A, R);
+            e = cudaGetLastError();
+        }
+    }
+    if (buf) {
+        const cudaError_t f = cudaFreeAsync(buf, s);
+        if (e == cudaSuccess) e = f;
+    }
+    SG_CUDA(e);
     return SG_OK;
 }
