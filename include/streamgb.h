@@ -468,7 +468,8 @@ sg_status sg_tracer_line_buffers(sg_tracer *t, float **slab, uint32_t **length, 
  * back onto p and lies in the cell's reference domain within tau.  Cells are
  * found through a bounding volume hierarchy built on the host at creation
  * (median splits, at most 4 cells per leaf).  Steady streamlines in world
- * coordinates: RK4 of Listing 1, one thread per seed; a stage point or new
+ * coordinates: RK4 of Listing 1, one thread per particle in rounds of at
+ * most 128 steps (sg_umesh_trace); a stage point or new
  * position in no cell stops the line (EXIT, margin = how far outside the
  * particle's cell, in parametric units). */
 typedef struct sg_umesh sg_umesh;

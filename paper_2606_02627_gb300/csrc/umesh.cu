@@ -414,7 +414,10 @@ struct URound {
     uint32_t seg;
 };
 
-__global__ void __launch_bounds__(256) umesh_round_kernel(UMeshView M, UTraceArgs A, URound R)
+// Built for 3 CTAs of 256 per SM (80 registers, with some spill): the
+// kernel waits on dependent loads, and 24 warps per SM hide more of that than
+// the 16 that 127 registers allow (measured on GB300: 5 % faster).
+__global__ void __launch_bounds__(256, 3) umesh_round_kernel(UMeshView M, UTraceArgs A, URound R)
 {
     const long long n = R.in ? (long long)*R.in_count : A.n;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
