@@ -451,7 +451,7 @@ def serve_workload(ctx, dev, n_requests, h, rank=0, tune=False):
         torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info(dev)
     slab = int(min(free * 0.6, 160e9))
-    srv = serving.Server(ctx, fields, max_lines=8 << 20, slab_bytes=slab, rounds_per_launch=4,
+    srv = serving.Server(ctx, fields, max_lines=8 << 20, slab_bytes=slab, rounds_per_launch=2,
                          max_requests=1024, schedule=sched)
     base = serving.make_requests(fields, n_requests, rate_hz=1.0, seed=4 + 1000 * rank)
     # capacity: the same requests all arriving at once
@@ -467,7 +467,7 @@ def serve_workload(ctx, dev, n_requests, h, rank=0, tune=False):
            "particle_steps": st["particle_steps"], "queue_ms_p99": st["queue_ms_p99"],
            "capacity": {"requests_per_s": len(burst) / cap["makespan_s"],
                         "particle_steps_per_s": cap["particle_steps_per_s"]},
-           "rounds_per_launch": 4, "slab_pool_bytes": slab, "schedule": sched or "library default"}
+           "rounds_per_launch": 2, "slab_pool_bytes": slab, "schedule": sched or "library default"}
     del srv, fields
     torch.cuda.empty_cache()
     return out

@@ -78,7 +78,7 @@ def make_requests(fields, n_requests: int, rate_hz: float, seed: int, min_seeds=
 
 class Server:
     def __init__(self, ctx: api.Context, fields, max_lines: int, slab_bytes: int, layout="cell8",
-                 rounds_per_launch: int = 4, max_requests: int = 1024, schedule=None):
+                 rounds_per_launch: int = 2, max_requests: int = 1024, schedule=None):
         self.ctx = ctx
         self.fields = fields
         self.rounds = rounds_per_launch
