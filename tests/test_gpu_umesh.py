@@ -130,3 +130,34 @@ def test_umesh_trace_on_a_side_stream_equals_default_stream(ctx, turb):
     torch.cuda.synchronize()
     assert torch.equal(b.offsets, alone.offsets)
     assert torch.equal(b.vertices, alone.vertices)
+
+
+def test_umesh_round_caps_cut_lines_at_their_prefix(ctx):
+    """The trace runs in rounds of at most 128 steps per particle.  Capped at
+    m steps, around and across those round boundaries, every line is the
+    first m + 1 vertices of the uncapped line, bit for bit, with its status
+    where it stopped earlier and MAXSTEPS otherwise.  Solid-body rotation
+    keeps the lines in the domain, so they run to the cap."""
+    from paper_2606_02627_gb300 import api
+    g = inputs.cube_grid(25)
+    F = inputs.rotation_field(g)
+    m = inputs.grid_mesh(g, F, kind="hex", jitter=0.1, seed=3)
+    mesh = api.UMesh(ctx, m)
+    seeds = torch.from_numpy(inputs.uniform_seeds(g, 256, 5, lo_cells=7.0, hi_cells=17.0))
+    dt = 0.25 / oracle.max_speed(F, g.spacing)
+    full = mesh.trace(seeds, dt, 600)
+    torch.cuda.synchronize()
+    f_off, f_v = full.offsets.cpu().numpy(), full.vertices.cpu().numpy()
+    f_len, f_st = np.diff(f_off), full.status.cpu().numpy() & 0x7F
+    assert (f_len == 601).sum() > 200                            # most lines run to the cap
+    for ms in (127, 128, 129, 255, 256, 257):
+        cap = mesh.trace(seeds, dt, ms)
+        torch.cuda.synchronize()
+        c_off, c_v = cap.offsets.cpu().numpy(), cap.vertices.cpu().numpy()
+        c_len, c_st = np.diff(c_off), cap.status.cpu().numpy() & 0x7F
+        np.testing.assert_array_equal(c_len, np.minimum(f_len, ms + 1))
+        for i in range(len(c_len)):
+            assert np.array_equal(c_v[c_off[i]:c_off[i + 1]], f_v[f_off[i]:f_off[i] + c_len[i]]), (ms, i)
+        stopped = f_len <= ms                                      # ended before the cap in both
+        assert (c_st[stopped] == f_st[stopped]).all()
+        assert (c_st[~stopped] == 1).all()                          # SG_LINE_MAXSTEPS
