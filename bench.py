@@ -72,9 +72,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end pass through host buffers (large workloads whose CSR would not fit a "
                          "page-locked host buffer)")
-    ap.add_argument("--config", default="steady", choices=["steady", "streak", "serve", "umesh", "plain"],
+    ap.add_argument("--config", default="steady",
+                    choices=["steady", "streak", "serve", "umesh", "plain", "bidir", "path", "pod"],
                     help="steady: brick-decomposed streamlines (the headline); streak: unsteady streaklines with "
-                         "time slices streamed from page-locked host memory")
+                         "time slices streamed from page-locked host memory; bidir, path, pod: bidirectional "
+                         "lines from a seed shape, path lines, partition over data (ranks emulated on one GPU)")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the rounds from the host (sg_tracer_trace_timed) instead of the CUDA graph, so that "
                          "a profiler sees every advection-kernel launch")
@@ -473,6 +475,218 @@ def serve_workload(ctx, dev, n_requests, h, rank=0, tune=False):
     return out
 
 
+def _cuda_ms(fn, steps, warmup, stream):
+    """Mean ms of fn() over `steps` calls after `warmup`, by CUDA events on `stream`."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _turbulence_512(ctx, dev, args):
+    """The headline's field: 512^3 synthetic turbulence (seed 1) on [0, 2pi]^3, with dt for h cells."""
+    import torch
+    from paper_2606_02627_gb300 import api, inputs
+    g = inputs.cube_grid(512)
+    F = inputs.turbulence_field(g, inputs.turbulence_modes(1), device=dev)
+    probe = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(4, 4, 4), dtype="f32")
+    probe.set_global(F)
+    dt = args.h / probe.max_speed()
+    probe.close()
+    torch.cuda.synchronize(dev)
+    return g, F, dt
+
+
+def run_bidir(args, rank, world, local):
+    """Bidirectional lines from a seed shape: on the headline's field (512^3 turbulence, 4x4x4 bricks,
+    CELL8 FP32), 1,048,576 seeds drawn on the device uniformly in the box of index [8, 503]^3
+    (sg_seeds_box, SplitMix64 seed 1), each traced forward and backward up to 1000 steps (RK4, h = 0.5
+    cell) and the two halves joined through the seed (sg_tracer_get_joined) into device buffers.
+    Step = seed kernel + upload + trace + join."""
+    import torch
+    from paper_2606_02627_gb300 import api
+    from paper_2606_02627_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    ctx = api.Context(local)
+    g, F, dt = _turbulence_512(ctx, dev, args)
+    n_seeds, max_steps = 1 << 20, 1000
+    lo = [g.origin[a] + 8 * g.spacing[a] for a in range(3)]
+    hi = [g.origin[a] + (g.dims[a] - 9) * g.spacing[a] for a in range(3)]
+    fld = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(4, 4, 4), dtype="f32", layout="cell8")
+    fld.set_global(F)
+    del F
+    tr = api.Tracer(ctx, fld, capacity=n_seeds, dt=dt, max_steps=max_steps, direction="both")
+    stream = torch.cuda.Stream(device=dev)
+    seeds = api.seeds_box(lo, hi, n_seeds, rank_seed(1, rank), stream=stream)
+    tr.upload_seeds(seeds, stream=stream)
+    tr.trace(stream=stream)
+    J = tr.get_joined(stream=stream)
+    stream.synchronize()
+    off, vert, sv = torch.empty_like(J.offsets), torch.empty_like(J.vertices), torch.empty_like(J.seed_vertex)
+
+    def step():
+        sd = api.seeds_box(lo, hi, n_seeds, rank_seed(1, rank), stream=stream)
+        tr.upload_seeds(sd, stream=stream)
+        tr.trace(stream=stream)
+        api.call("sg_tracer_get_joined", tr.h, None, None, api._ptr(off), api._ptr(vert), api._ptr(sv),
+                 api._stream(stream))
+
+    ms = _cuda_ms(step, args.steps, args.warmup, stream)
+    steps = tr.total_steps(stream=stream)
+    tr.check(stream=stream)
+    out = {"metric": METRIC + " (bidirectional lines)", "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "bidirectional: 512^3 FP32 turbulence (seed 1), 4x4x4 bricks, CELL8; 1048576 "
+                                  "seeds uniform in index box [8, 503]^3 drawn on the device (sg_seeds_box), each "
+                                  "traced forward and backward up to 1000 steps, RK4 h=0.5 cell, halves joined "
+                                  "through the seed", "lines": 2 * n_seeds},
+           "particle_steps_per_step": steps, "joined_vertices": int(J.vertices.shape[0])}
+    print(json.dumps(out))
+
+
+def run_path(args, rank, world, local):
+    """Path lines: every seed released once at time 0 and followed through the unsteady field of the
+    streakline workload (64 time slices of 256^3 FP32 turbulence, seed 3, streamed from page-locked host
+    memory into three resident slots on a side stream), 1,048,576 seeds uniform in the interior (seed 3),
+    RK4 h = 0.5 cell (dt = the slice interval), 63 steps with the field linear in time between slices.
+    Step = the 64 slice uploads + seeds + 63 advection steps + the CSR of the lines in device buffers."""
+    import torch
+    from paper_2606_02627_gb300 import api, inputs
+    from paper_2606_02627_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    n, n_slices, n_seeds = 256, 64, 1 << 20
+    g = inputs.cube_grid(n)
+    modes = inputs.turbulence_modes(3)
+    ctx = api.Context(local)
+    host = torch.empty((n_slices, n, n, n, 3), dtype=torch.float32).pin_memory()
+    vref = 0.0
+    sp = torch.tensor(g.spacing, device=dev, dtype=torch.float32)
+    for s_ in range(n_slices):
+        F = inputs.turbulence_field(g, modes, time_slice=s_, n_slices=n_slices, device=dev)
+        vref = max(vref, float((F / sp).norm(dim=-1).max()))
+        host[s_].copy_(F)
+        del F
+    dt = args.h / vref
+    steps_cap = n_slices - 1
+    seeds = torch.from_numpy(inputs.uniform_seeds(g, n_seeds, rank_seed(3, rank), lo_cells=1.0)).to(dev)
+    fld = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=(2, 2, 2), dtype="f32", layout="linear", n_slots=3,
+                    slice_dt=dt)
+    tr = api.Tracer(ctx, fld, capacity=n_seeds, dt=dt, max_steps=steps_cap, mode="pathline")
+    main_s = torch.cuda.Stream(device=dev)
+    side = torch.cuda.Stream(device=dev)
+    nl, nv = [0], [0]
+    bufs = {}
+
+    def run_once():
+        fld.stream_slice(0, host[0], stream=side)
+        fld.stream_slice(1, host[1], stream=side)
+        tr.upload_seeds(seeds, stream=main_s)
+        for j in range(steps_cap):
+            # step j+1 spans times j dt .. (j+1) dt: it needs slices j and j+1
+            if j + 2 < n_slices:
+                fld.stream_slice(j + 2, host[j + 2], stream=side)
+            tr.step(1, sync=False, stream=main_s)
+        if bufs:
+            api.call("sg_tracer_get_lines", tr.h, None, None, api._ptr(bufs["off"]), api._ptr(bufs["v"]),
+                     api._ptr(bufs["st"]), None, None, api._stream(main_s))
+
+    run_once()
+    torch.cuda.synchronize(dev)
+    nl[0], nv[0] = tr.sizes(stream=main_s)
+    bufs.update(off=torch.empty(nl[0] + 1, dtype=torch.int64, device=dev),
+                v=torch.empty((max(nv[0], 1), 3), dtype=torch.float32, device=dev),
+                st=torch.empty(max(nl[0], 1), dtype=torch.uint8, device=dev))
+    steps = tr.total_steps(stream=main_s)
+
+    def timed_once():
+        run_once()
+        main_s.wait_stream(side)
+
+    ms = _cuda_ms(timed_once, args.steps, args.warmup, main_s)
+    h2d = n_slices * n ** 3 * 12
+    out = {"metric": METRIC + " (path lines)", "value": steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"path lines: {n_slices} slices of {n}^3 FP32 turbulence (seed 3) streamed from "
+                                  f"page-locked host memory, {n_seeds} seeds released at t=0, {steps_cap} steps, "
+                                  f"RK4 h={args.h} cell, field linear in time", "slots": 3, "bricks": "2x2x2",
+                      "layout": "linear"},
+           "particle_steps_per_step": steps, "h2d_bytes_per_step": h2d, "h2d_gbs": h2d / (ms / 1e3) / 1e9,
+           "lines": nl[0], "vertices": nv[0]}
+    print(json.dumps(out))
+
+
+def run_pod(args, rank, world, local):
+    """Partition over data with its ranks emulated on one GPU: the headline's field (512^3 turbulence,
+    4x4x4 bricks, CELL8 FP32), 262,144 seeds uniform (seed 1), max 1000 steps, RK4 h = 0.5 cell; the 64
+    bricks split over 4 ranks (pod.partition_bricks), one tracer per rank advancing only its own
+    particles and handing the others to their owners between rounds (sg_tracer_pod_*, device copies
+    between the ranks' buffers), then the ranks' lines merged.  Timed beside the undivided trace of the
+    same seeds: the ratio is what the exchange costs when every rank shares one GPU."""
+    import torch
+    from paper_2606_02627_gb300 import api, pod
+    from paper_2606_02627_gb300 import build as _build
+    from paper_2606_02627_gb300 import inputs
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    ctx = api.Context(local)
+    g, F, dt = _turbulence_512(ctx, dev, args)
+    n_seeds, max_steps, ranks = 1 << 18, 1000, 4
+    bricks = (4, 4, 4)
+    fld = api.Field(ctx, g.dims, g.origin, g.spacing, bricks=bricks, dtype="f32", layout="cell8")
+    fld.set_global(F)
+    del F
+    seeds = torch.from_numpy(inputs.uniform_seeds(g, n_seeds, rank_seed(1, rank))).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    undivided = api.Tracer(ctx, fld, capacity=n_seeds, dt=dt, max_steps=max_steps)
+
+    def run_undivided():
+        undivided.upload_seeds(seeds)
+        undivided.trace()
+
+    owner = pod.partition_bricks(bricks, ranks)
+    engines = [pod.GpuEngine(api.Tracer(ctx, fld, capacity=n_seeds, dt=dt, max_steps=max_steps), owner, r, ranks)
+               for r in range(ranks)]
+    rounds = [0]
+
+    def run_pod_once():
+        for e in engines:
+            e.tr.upload_seeds(seeds)
+        rounds[0] = pod.LocalTransport.trace_local(engines)
+
+    ms_u = _cuda_ms(run_undivided, args.steps, args.warmup, stream)
+    ms_p = _cuda_ms(run_pod_once, args.steps, args.warmup, stream)
+    steps = undivided.total_steps()
+    got = engines[0].tr.get_lines()
+    ref = undivided.get_lines()
+    torch.cuda.synchronize(dev)
+    same = bool(torch.equal(got.offsets, ref.offsets) and torch.equal(got.vertices, ref.vertices))
+    out = {"metric": METRIC + " (partition over data, 4 ranks emulated on one GPU)", "value": steps / (ms_p / 1e3),
+           "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_p,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "partition over data: 512^3 FP32 turbulence (seed 1), 64 bricks (4x4x4) over 4 "
+                                  "ranks emulated as tracers on one GPU, CELL8, 262144 seeds, max 1000 steps, RK4 "
+                                  "h=0.5 cell", "ranks": ranks, "exchange_rounds": rounds[0]},
+           "particle_steps_per_step": steps, "undivided": {"value": steps / (ms_u / 1e3), "ms_per_step": ms_u},
+           "merged_lines_equal_undivided": same}
+    print(json.dumps(out))
+
+
 def run_serve(args, rank, world, local):
     """The serving workload on its own, with the autotuner's schedule (config 5)."""
     import torch
@@ -567,6 +781,12 @@ def main():
         return run_serve(args, rank, world, local)
     if args.config == "umesh":
         return run_umesh(args, rank, world, local)
+    if args.config == "bidir":
+        return run_bidir(args, rank, world, local)
+    if args.config == "path":
+        return run_path(args, rank, world, local)
+    if args.config == "pod":
+        return run_pod(args, rank, world, local)
     import numpy as np
     import torch
 
