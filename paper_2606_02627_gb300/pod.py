@@ -150,7 +150,10 @@ class LocalTransport:
             acc = bufs[0][key][0].clone()
             for b in bufs[1:]:
                 t = b[key][0].to(acc.device)
-                acc = torch.minimum(acc, t) if op == "min" else torch.maximum(acc, t)
+                if op == "min":
+                    torch.minimum(acc, t, out=acc)
+                else:
+                    torch.maximum(acc, t, out=acc)
             for b in bufs:
                 b[key][0].copy_(acc)
         return rounds
