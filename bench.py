@@ -924,6 +924,23 @@ def main():
         ms, tot_all = reduce_over_ranks(ms, tot, dist, dev)
         ok = tr.check(stream=stream)
         bytes_out = off.numel() * 8 + nv * 12 + nl
+        if host_out:
+            # the copy rate into the step's own page-locked output (its first 2 GiB), after the timed region:
+            # sets a slow host buffer apart from a slow pipeline
+            n = min(vert.numel(), 1 << 29)
+            src = torch.empty(n, dtype=torch.float32, device=dev)
+            best = None
+            for _ in range(3):
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                with torch.cuda.stream(stream):
+                    vert.view(-1)[:n].copy_(src, non_blocking=True)
+                c1.record(stream)
+                c1.synchronize()
+                best = c0.elapsed_time(c1) if best is None else min(best, c0.elapsed_time(c1))
+            timed.out_buffer_gbs = n * 4 / (best / 1e3) / 1e9
+            del src
         return ms, tot, tot_all, bytes_out
 
     results = {}
@@ -1024,6 +1041,7 @@ def main():
         # step's trace, so the step takes about max(trace, D2H copy) plus the pipeline's fill and drain)
         e2e.update(copy_rates(dev))
         e2e["d2h_ms_per_step"] = d2h / (e2e["d2h_gbs"] * 1e9) * 1e3
+        e2e["d2h_gbs_into_output"] = getattr(timed, "out_buffer_gbs", None)
     del tr, fld
     torch.cuda.empty_cache()
 
