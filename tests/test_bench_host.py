@@ -54,3 +54,26 @@ def test_traffic_needs_matching_hash(fake_root):
     src.write_text(src.read_text() + "\n// edit\n")
     assert bench.traffic_per_step("f32", "async") is None
     assert bench.traffic_per_step("f32", "missing_tag") is None
+
+
+def test_cpu_baseline_sizing():
+    """The CPU baseline traces a prefix of the seeds: a calibration run, then
+    rescaled runs until the sample takes at least half the target time (or
+    every seed); with n_seeds it traces exactly that prefix."""
+    import numpy as np
+    from paper_2606_02627_gb300 import inputs
+    import oracle
+    g = inputs.cube_grid(17)
+    F = inputs.turbulence_field(g, inputs.turbulence_modes(3, n_modes=16, kmax=2)).numpy()
+    seeds = inputs.uniform_seeds(g, 4000, 3)
+    dt = 0.5 / oracle.max_speed(F, g.spacing)
+    rate, cores, n, steps, secs = bench.cpu_oracle_rate(F, g, seeds, dt, 60, 0.2, nthreads=2)
+    assert cores == 2 and 0 < n <= len(seeds) and steps > 0 and rate > 0
+    assert secs >= 0.1 or n == len(seeds)
+    ref = oracle.trace_streamlines(F, g.origin, g.spacing, seeds[:n], dt, 60, eps=1e-6, nthreads=2)
+    assert steps == int(ref.steps().sum())
+    rate2, _, n2, steps2, _ = bench.cpu_oracle_rate(F, g, seeds, dt, 60, 0.2, nthreads=2, n_seeds=123)
+    assert n2 == 123 and rate2 > 0
+    assert steps2 == int(oracle.trace_streamlines(F, g.origin, g.spacing, seeds[:123], dt, 60, eps=1e-6,
+                                                  nthreads=2).steps().sum())
+    assert np.isfinite(rate) and np.isfinite(rate2)
