@@ -48,7 +48,7 @@ def candidates(max_threads_per_sm: int = 2048, regs_limit_threads: int = 1024):
     most 256 threads: the kernels are built for that (their register budget)."""
     out = []
     for block, threads, spr, drain in itertools.product((64, 128, 256), (256, 384, 512, 768, 1024),
-                                                         (128, 256, 512), (0, -1)):
+                                                         (256, 512, 1024, 2048), (0, -1)):
         if threads > min(max_threads_per_sm, regs_limit_threads) or threads % block:
             continue
         out.append((block, threads // block, spr, drain))
