@@ -255,7 +255,7 @@ typedef struct {
                               register budget)                                   */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent grid                     */
     int32_t steps_per_round; /* steps a particle may take in one round before it is
-                                re-queued in its own brick (0 = default: 256 for the
+                                re-queued in its own brick (0 = default: 1024 for the
                                 decoupled-lane kernel, 128 otherwise)               */
     int32_t max_rounds;    /* round cap of one trace / step call (0 = max_steps + 2,
                               which only a fault can reach).  A call stopped by it

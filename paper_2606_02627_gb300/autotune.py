@@ -38,7 +38,7 @@ from . import api
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "streamgb", "autotune.json")
 LAYOUTS = ("cell8", "tiled4", "linear")
-DEFAULT_DECOUPLED = (256, 3, 256, 0)          # the library's schedule of the decoupled-lane kernel
+DEFAULT_DECOUPLED = (256, 3, 1024, 0)         # the library's schedule of the decoupled-lane kernel
 BRICKS = ((4, 4, 4), (2, 2, 2), (8, 8, 8))
 
 
@@ -228,7 +228,7 @@ def tune_structure(ctx: api.Context, source: torch.Tensor, grid, dtype: str, see
     # stage 2: schedules of the best structures
     pairs = [(s, c) for s in best for c in (cands or candidates())]
     pairs.sort(key=lambda x: (x[0][0], x[0][1]))
-    # the library's schedule of the decoupled-lane kernel: 3 CTAs of 256, 256 steps per round, its drain
+    # the library's schedule of the decoupled-lane kernel: 3 CTAs of 256, 1024 steps per round, its drain
     default_pair = (default_struct, DEFAULT_DECOUPLED)
     ranked_p, hist_p = _halving(pairs, seeds, first, rounds,
                                 lambda sc, p: run_structure(sc[0], p, schedule_of(sc[1])), log, "schedule",
