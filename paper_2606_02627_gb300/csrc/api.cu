@@ -804,9 +804,9 @@ extern "C" sg_status sg_tracer_get_lines_overlapped(sg_tracer *t, int64_t *n_lin
         t->ovl_buf[k] = nullptr;
         t->ovl_bytes[k] = 0;
         cudaError_t ae = cudaMalloc(&t->ovl_buf[k], bytes);
+        if (ae != cudaSuccess) t->ovl_buf[k] = nullptr;   // nothing to free later
         if (ae == cudaErrorMemoryAllocation && k == 1) {
             (void)cudaGetLastError();            // not sticky: the first buffer serves from now on
-            t->ovl_buf[k] = nullptr;
             t->ovl_single = true;
             k = 0;
             if (need > t->ovl_bytes[0]) {
@@ -814,7 +814,9 @@ extern "C" sg_status sg_tracer_get_lines_overlapped(sg_tracer *t, int64_t *n_lin
                 if (t->ovl_buf[0]) SG_CUDA(cudaFree(t->ovl_buf[0]));
                 t->ovl_buf[0] = nullptr;
                 t->ovl_bytes[0] = 0;
-                SG_CUDA(cudaMalloc(&t->ovl_buf[0], bytes));
+                const cudaError_t a0 = cudaMalloc(&t->ovl_buf[0], bytes);
+                if (a0 != cudaSuccess) t->ovl_buf[0] = nullptr;
+                SG_CUDA(a0);
                 t->ovl_bytes[0] = bytes;
             }
         } else {
