@@ -255,8 +255,10 @@ typedef struct {
                               register budget)                                   */
     int32_t blocks_per_sm; /* CTAs per SM of the persistent grid                     */
     int32_t steps_per_round; /* steps a particle may take in one round before it is
-                                re-queued in its own brick (0 = default: 1024 for the
-                                decoupled-lane kernel, 128 otherwise)               */
+                                re-queued in its own brick (0 = default: for the
+                                decoupled-lane kernel 1024 when the capacity is at
+                                least 4 x SMs x 768 particles, else 256; 128 for
+                                the other kernels)                                  */
     int32_t max_rounds;    /* round cap of one trace / step call (0 = max_steps + 2,
                               which only a fault can reach).  A call stopped by it
                               returns (or its sg_tracer_check reports)
